@@ -1,0 +1,219 @@
+"""FP64 sequential CPU oracle for SNAP-tFDP -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never calls it and
+shares no code with it: the C source ``snap_oracle.c`` restates every formula
+from the paper (Table 1, Eq. 2, Eq. 4, Section 3.3, Algorithm 1, the NP metric
+of Section 4.1) independently of the CUDA kernels.
+
+Parity status per function:
+  philox4x32_10               pinned (published known-answer vectors)
+  uniform_negative            pinned (closed-form end points, exclusion, chi^2)
+  pair_terms                  pinned (finite differences of the energies, Eq. 2)
+  objective / objective_sampled pinned (n = 2 closed form, finite-difference
+                              gradient, sampled vs exact)
+  exact_gradient              pinned (finite differences of the objective)
+  epoch_displacement          pinned (Monte-Carlo mean -> -2 grad U, Section 3.3)
+  seq (Algorithm 1)           pinned (two-node closed form, n = 2 forced draw,
+                              centroid invariance, rotation equivariance,
+                              actual-vs-effective energy of Fig. 3)
+  sync                        pinned (S = 1 equals Y + eta * displacement;
+                              chunk bounds by hand; cap by closed form)
+  neighborhood_preservation   pinned (hand-computed 6-node case, lattice case)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "snap_oracle.c")
+_LIB = os.path.join(_HERE, "libsnap_oracle.so")
+_lib = None
+
+ALPHA = 0.1
+BETA = 8.0
+GAMMA = 2.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no fused multiply-add)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    i32, i64, u32, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+    lib.oracle_philox4x32_10.argtypes = [P, P, P]
+    lib.oracle_philox4x32_10.restype = None
+    lib.oracle_edge_word.argtypes = [u64, u32, u32, u64]
+    lib.oracle_edge_word.restype = u32
+    lib.oracle_uniform_negative.argtypes = [u32, i32, i32]
+    lib.oracle_uniform_negative.restype = i32
+    lib.oracle_step_size.argtypes = [i32, f64, f64, i32, i32]
+    lib.oracle_step_size.restype = f64
+    lib.oracle_pair_terms.argtypes = [f64, f64, P]
+    lib.oracle_pair_terms.restype = None
+    lib.oracle_seq.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, u64, i64, P]
+    lib.oracle_seq.restype = ctypes.c_int
+    lib.oracle_sync_chunk_bounds.argtypes = [P, i32, i32, P]
+    lib.oracle_sync_chunk_bounds.restype = None
+    lib.oracle_epoch_displacement.argtypes = [P, P, i32, P, i32, i32, u64, P]
+    lib.oracle_epoch_displacement.restype = ctypes.c_int
+    lib.oracle_sync.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, f64]
+    lib.oracle_sync.restype = ctypes.c_int
+    lib.oracle_objective.argtypes = [P, P, i32, P, i32, P]
+    lib.oracle_objective.restype = ctypes.c_int
+    lib.oracle_objective_sampled.argtypes = [P, P, i32, P, i32, i64, u64, P]
+    lib.oracle_objective_sampled.restype = ctypes.c_int
+    lib.oracle_exact_gradient.argtypes = [P, P, i32, P, i32, P]
+    lib.oracle_exact_gradient.restype = ctypes.c_int
+    lib.oracle_neighborhood_preservation.argtypes = [P, P, i32, P, P, i32]
+    lib.oracle_neighborhood_preservation.restype = f64
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(row_ptr, col_idx):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    return rp, ci
+
+
+def _positions(Y) -> np.ndarray:
+    return np.array(Y, dtype=np.float64, order="C").reshape(-1, 2)
+
+
+def _sched(schedule):
+    if schedule is None:
+        schedule = {}
+    kind = int(schedule.get("kind", 0))
+    eta0 = float(schedule.get("eta0", 1.0))
+    eta_min = float(schedule.get("eta_min", eta0 * 1e-3))
+    total = int(schedule.get("total_epochs", 30))
+    return kind, eta0, eta_min, total
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def edge_word(e: int, t: int, w: int, seed: int) -> int:
+    return int(_load().oracle_edge_word(e, t, w, seed))
+
+
+def uniform_negative(word: int, i: int, n: int) -> int:
+    return int(_load().oracle_uniform_negative(word, i, n))
+
+
+def step_size(schedule, t: int) -> float:
+    kind, eta0, eta_min, total = _sched(schedule)
+    return float(_load().oracle_step_size(kind, eta0, eta_min, total, t))
+
+
+def pair_terms(dx: float, dy: float) -> np.ndarray:
+    """{Fa_x, Fa_y, Fr_x, Fr_y, Ua, Ur} for y_i - y_other = (dx, dy)."""
+    out = np.zeros(6)
+    _load().oracle_pair_terms(dx, dy, _p(out))
+    return out
+
+
+def seq(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, shuffle_seed=None,
+        epoch_begin=0, max_edges_per_epoch=-1, return_energy=False, shuffle=True):
+    """Algorithm 1 (sequential, immediate updates).  Returns the final (n,2) float64.
+
+    shuffle=False visits the directed edges in CSR order."""
+    rp, ci = _csr(row_ptr, col_idx)
+    Y = _positions(Y0).copy()
+    kind, eta0, eta_min, total = _sched(schedule)
+    en = np.zeros(max(epochs, 1))
+    shuffle_seed = seed ^ 0x5DEECE66D if shuffle_seed is None else shuffle_seed
+    rc = _load().oracle_seq(_p(rp), _p(ci), n, _p(Y), epoch_begin, epochs, k, kind, eta0, eta_min,
+                            total, seed, int(bool(shuffle)), shuffle_seed, max_edges_per_epoch,
+                            _p(en) if return_energy else None)
+    if rc != 0:
+        raise MemoryError("oracle_seq failed to allocate")
+    return (Y, en[:epochs]) if return_energy else Y
+
+
+def sync_chunk_bounds(row_ptr, n, S) -> np.ndarray:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    out = np.zeros(S + 1, dtype=np.int32)
+    _load().oracle_sync_chunk_bounds(_p(rp), n, S, _p(out))
+    return out
+
+
+def epoch_displacement(row_ptr, col_idx, n, Y, t, k, seed) -> np.ndarray:
+    rp, ci = _csr(row_ptr, col_idx)
+    Yd = _positions(Y)
+    D = np.zeros((n, 2))
+    _load().oracle_epoch_displacement(_p(rp), _p(ci), n, _p(Yd), t, k, seed, _p(D))
+    return D
+
+
+def sync(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, substeps=1, cap=0.0,
+         epoch_begin=0):
+    """Chunked synchronous (Jacobi) epochs.  Returns the final (n,2) float64."""
+    rp, ci = _csr(row_ptr, col_idx)
+    Y = _positions(Y0).copy()
+    kind, eta0, eta_min, total = _sched(schedule)
+    rc = _load().oracle_sync(_p(rp), _p(ci), n, _p(Y), epoch_begin, epochs, k, kind, eta0, eta_min,
+                             total, seed, substeps, cap)
+    if rc != 0:
+        raise MemoryError("oracle_sync failed to allocate")
+    return Y
+
+
+def objective(row_ptr, col_idx, n, Y, k) -> dict:
+    rp, ci = _csr(row_ptr, col_idx)
+    Yd = _positions(Y)
+    out = np.zeros(4)
+    _load().oracle_objective(_p(rp), _p(ci), n, _p(Yd), k, _p(out))
+    return dict(attr=out[0], rep=out[1], total=out[2], rep_designed=out[3])
+
+
+def objective_sampled(row_ptr, col_idx, n, Y, k, pairs, seed) -> dict:
+    rp, ci = _csr(row_ptr, col_idx)
+    Yd = _positions(Y)
+    out = np.zeros(4)
+    _load().oracle_objective_sampled(_p(rp), _p(ci), n, _p(Yd), k, pairs, seed, _p(out))
+    return dict(attr=out[0], rep=out[1], total=out[2])
+
+
+def exact_gradient(row_ptr, col_idx, n, Y, k) -> np.ndarray:
+    rp, ci = _csr(row_ptr, col_idx)
+    Yd = _positions(Y)
+    G = np.zeros((n, 2))
+    _load().oracle_exact_gradient(_p(rp), _p(ci), n, _p(Yd), k, _p(G))
+    return G
+
+
+def neighborhood_preservation(row_ptr, col_idx, n, Y, nodes=None) -> float:
+    rp, ci = _csr(row_ptr, col_idx)
+    Yd = _positions(Y)
+    if nodes is None:
+        return float(_load().oracle_neighborhood_preservation(_p(rp), _p(ci), n, _p(Yd), None, 0))
+    nd = np.ascontiguousarray(nodes, dtype=np.int32)
+    return float(_load().oracle_neighborhood_preservation(_p(rp), _p(ci), n, _p(Yd), _p(nd), nd.size))

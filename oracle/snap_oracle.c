@@ -1,0 +1,569 @@
+/*
+ * snap_oracle.c -- sequential FP64 CPU oracle for SNAP-tFDP
+ * ("Massively Scalable Graph Layouts via Sparse Negative Sampling").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the smoke check and the bench's CPU
+ * baseline leg do.  It shares no code, header or constant table with the CUDA
+ * path: every definition below is written out again from the paper.
+ *
+ * What it computes (citations are to the paper):
+ *   - t-FDP forces and energies, Table 1 and Eq. 2 (alpha=0.1, beta=8, gamma=2,
+ *     Section 3.1).
+ *   - The degree-weighted objective, Eq. 4, with the weight the edge-centric
+ *     sampler realises, (d_i+d_j)/(2(|V|-1)) (Section 3.3), and the designed
+ *     weight of Eq. 5, (d_i+d_j)/(2|V|), for reference.
+ *   - Algorithm 1 (edge-centric negative sampling), sequential, immediate
+ *     updates, the directed edge list shuffled once before the epoch loop.
+ *   - A synchronous (chunked Jacobi) variant: positions frozen within a chunk
+ *     of rows, all forces of the chunk summed, then applied.  The paper has no
+ *     such mode; it is the deterministic reference for the library's
+ *     synchronous mode.
+ *   - Neighbourhood preservation NP with r = 2 (Section 4.1, Metrics).
+ *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As
+ *     Easy as 1, 2, 3", SC'11) for the negative draws.
+ *
+ * Readings of the paper that the code depends on:
+ *   - Signs.  Table 1 prints attraction along +e_ij and repulsion along -e_ij
+ *     with e_ij = (y_i - y_j)/|y_i - y_j|, and Algorithm 1 adds eta*F to y_i.
+ *     Taken literally that pushes neighbours apart.  Section 3.1 states the
+ *     physics (adjacent vertices drawn together, all vertices repel) and
+ *     Eq. 2 states F = -grad U, so the force ON i is
+ *        attraction  -alpha (1 + beta/(1+r^2)) (y_i - y_j)
+ *        repulsion   +(1+r^2)^-gamma (y_i - y_s)
+ *     and the partner always receives the opposite vector.
+ *   - The attractive force of one step is evaluated once, from the positions
+ *     before the step, and applied to both endpoints.
+ *   - The loop index of the inner negative-sample loop of Algorithm 1 reuses
+ *     the name j; it is read as a separate counter m = 0..k-1.
+ *   - Negatives are uniform over V \ {i}: only the source is excluded; the
+ *     draw may hit j and may repeat.
+ *   - The step size decays linearly per epoch (Section 3.3 only says it
+ *     follows standard practice and decays; Algorithm 1 updates it once per
+ *     epoch): eta_t = max(eta0 * (1 - t/T), eta_min).
+ *   - Random words: word w of the stream of directed edge e in epoch t is
+ *     component (w mod 4) of Philox4x32-10(counter = (e_lo, e_hi, t, w div 4),
+ *     key = (seed_lo, seed_hi)); e is the edge's index in the row-major CSR.
+ *     Negative m of edge e = (i, j) uses word m:  u = floor(word*(n-1)/2^32),
+ *     s = u + (u >= i).
+ *
+ * Build: plain C11, compiled with -ffp-contract=off so that no multiply-add
+ * is fused (the rotation test relies on exact IEEE rounding of each op).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* t-FDP parameters recommended by the t-FDP authors and used by the paper
+ * (Section 3.1, "t-FDP Model"). */
+static const double ORC_ALPHA = 0.1;
+static const double ORC_BETA = 8.0;
+/* gamma = 2 is written into the formulas below: (1+r^2)^-2 and
+ * U^r = (1+r^2)^(1-gamma) / (2(gamma-1)) = 1 / (2(1+r^2)). */
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11): a 10-round Feistel-like bijection   */
+/* on 4x32-bit counters keyed by 2x32-bit keys.                              */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    /* round multipliers and Weyl key increments of Philox4x32 */
+    const uint64_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += weyl0;
+            k1 += weyl1;
+        }
+        uint64_t p0 = mult0 * (uint64_t)x0;
+        uint64_t p1 = mult1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Word w of the random stream of directed edge e in epoch t. */
+uint32_t oracle_edge_word(uint64_t e, uint32_t t, uint32_t w, uint64_t seed)
+{
+    uint32_t ctr[4] = {(uint32_t)e, (uint32_t)(e >> 32), t, w / 4u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[w % 4u];
+}
+
+/* Uniform draw from V \ {i} (Algorithm 1, "Sample y_s ~ Uniform(Y \ {y_i})"). */
+int32_t oracle_uniform_negative(uint32_t word, int32_t i, int32_t n)
+{
+    uint32_t u = (uint32_t)(((uint64_t)word * (uint64_t)(uint32_t)(n - 1)) >> 32);
+    return (int32_t)(u + (u >= (uint32_t)i ? 1u : 0u));
+}
+
+/* Step size of epoch t (paper: "decaying over epochs", updated once per epoch). */
+double oracle_step_size(int32_t kind, double eta0, double eta_min, int32_t total_epochs, int32_t t)
+{
+    if (kind == 1)
+        return eta0;                       /* constant */
+    double T = (double)(total_epochs > 0 ? total_epochs : 1);
+    double eta = eta0 * (1.0 - (double)t / T);
+    return eta > eta_min ? eta : eta_min;  /* linear decay with a floor */
+}
+
+/* Force on i for the displacement d = y_i - y_other, and the two energies.
+ * out = {Fa_x, Fa_y, Fr_x, Fr_y, Ua, Ur}.                                  */
+void oracle_pair_terms(double dx, double dy, double out[6])
+{
+    double r2 = dx * dx + dy * dy;
+    double one_r2 = 1.0 + r2;
+    /* Table 1, t-FDP attraction: magnitude alpha (r + beta r / (1+r^2)),
+     * pulling i toward the neighbour. */
+    double ca = ORC_ALPHA * (1.0 + ORC_BETA / one_r2);
+    /* Table 1, t-FDP repulsion: magnitude r / (1+r^2)^gamma, gamma = 2,
+     * pushing i away from the sample. */
+    double cr = 1.0 / (one_r2 * one_r2);
+    out[0] = -ca * dx;
+    out[1] = -ca * dy;
+    out[2] = cr * dx;
+    out[3] = cr * dy;
+    /* Eq. 2: the energies whose negative gradients are the forces above. */
+    out[4] = ORC_ALPHA * (0.5 * r2 + 0.5 * ORC_BETA * log1p(r2));
+    out[5] = 0.5 / one_r2;
+}
+
+static void attraction_on_i(double dx, double dy, double *fx, double *fy)
+{
+    double r2 = dx * dx + dy * dy;
+    double ca = ORC_ALPHA * (1.0 + ORC_BETA / (1.0 + r2));
+    *fx = -ca * dx;
+    *fy = -ca * dy;
+}
+
+static void repulsion_on_i(double dx, double dy, double *fx, double *fy)
+{
+    double r2 = dx * dx + dy * dy;
+    double one_r2 = 1.0 + r2;
+    double cr = 1.0 / (one_r2 * one_r2);
+    *fx = cr * dx;
+    *fy = cr * dy;
+}
+
+static double energy_attr(double dx, double dy)
+{
+    double r2 = dx * dx + dy * dy;
+    return ORC_ALPHA * (0.5 * r2 + 0.5 * ORC_BETA * log1p(r2));
+}
+
+static double energy_rep(double dx, double dy)
+{
+    double r2 = dx * dx + dy * dy;
+    return 0.5 / (1.0 + r2);
+}
+
+static int32_t *row_of_edges(const int64_t *row_ptr, int32_t n)
+{
+    int64_t nnz = row_ptr[n];
+    int32_t *src = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!src)
+        return NULL;
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            src[e] = i;
+    return src;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1, sequential, immediate updates.                              */
+/* Y is n x 2 row-major doubles, updated in place.  shuffle = 0 keeps the   */
+/* CSR order (one of the orders a shuffle can produce).                     */
+/* max_edges_per_epoch < 0 processes every edge; otherwise only that many   */
+/* edges of the shuffled order are visited in each epoch (a timing sample). */
+/* actual_energy (nullable, one value per epoch): half the sum of U^a over  */
+/* the visited directed edges plus U^r over the drawn pairs, each taken at  */
+/* the moment of its update (Section 3.3, "actual energy").                 */
+/* Returns 0, or -1 on allocation failure.                                  */
+/* ------------------------------------------------------------------------ */
+int oracle_seq(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double *Y,
+               int32_t epoch_begin, int32_t epochs, int32_t k,
+               int32_t sched_kind, double eta0, double eta_min, int32_t total_epochs,
+               uint64_t seed, int32_t shuffle, uint64_t shuffle_seed, int64_t max_edges_per_epoch,
+               double *actual_energy)
+{
+    int64_t nnz = row_ptr[n];
+    int32_t *src = row_of_edges(row_ptr, n);
+    int64_t *order = (int64_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int64_t));
+    if (!src || !order) {
+        free(src);
+        free(order);
+        return -1;
+    }
+    /* "Randomly shuffle edge list E" -- once, before the epoch loop
+     * (Fisher-Yates, driven by its own Philox stream). */
+    for (int64_t e = 0; e < nnz; ++e)
+        order[e] = e;
+    uint32_t skey[2] = {(uint32_t)shuffle_seed, (uint32_t)(shuffle_seed >> 32)};
+    for (int64_t p = shuffle ? nnz - 1 : 0; p > 0; --p) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0xFFFFFFFEu, 0u};
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, skey, w);
+        uint64_t r64 = ((uint64_t)w[0] << 32) | w[1];
+        int64_t q = (int64_t)(r64 % (uint64_t)(p + 1));
+        int64_t tmp = order[p];
+        order[p] = order[q];
+        order[q] = tmp;
+    }
+    int64_t visit = (max_edges_per_epoch >= 0 && max_edges_per_epoch < nnz) ? max_edges_per_epoch : nnz;
+
+    for (int32_t ep = 0; ep < epochs; ++ep) {
+        int32_t t = epoch_begin + ep;
+        double eta = oracle_step_size(sched_kind, eta0, eta_min, total_epochs, t);
+        double energy = 0.0;
+        for (int64_t q = 0; q < visit; ++q) {
+            int64_t e = order[q];
+            int32_t i = src[e];
+            int32_t j = col_idx[e];
+            double *yi = Y + 2 * (int64_t)i;
+            double *yj = Y + 2 * (int64_t)j;
+            double dx = yi[0] - yj[0], dy = yi[1] - yj[1];
+            double fx, fy;
+            if (actual_energy)
+                energy += energy_attr(dx, dy);
+            attraction_on_i(dx, dy, &fx, &fy);
+            yi[0] += eta * fx;
+            yi[1] += eta * fy;
+            yj[0] -= eta * fx;
+            yj[1] -= eta * fy;
+            for (int32_t m = 0; m < k; ++m) {
+                uint32_t word = oracle_edge_word((uint64_t)e, (uint32_t)t, (uint32_t)m, seed);
+                int32_t s = oracle_uniform_negative(word, i, n);
+                double *ys = Y + 2 * (int64_t)s;
+                double sx = yi[0] - ys[0], sy = yi[1] - ys[1];
+                if (actual_energy)
+                    energy += energy_rep(sx, sy);
+                repulsion_on_i(sx, sy, &fx, &fy);
+                yi[0] += eta * fx;
+                yi[1] += eta * fy;
+                ys[0] -= eta * fx;
+                ys[1] -= eta * fy;
+            }
+        }
+        if (actual_energy)
+            actual_energy[ep] = 0.5 * energy;
+    }
+    free(src);
+    free(order);
+    return 0;
+}
+
+/* Row boundaries of the synchronous chunks: chunk c holds rows
+ * [bound[c], bound[c+1]); bound[c] for 0 < c < S is the first row r with
+ * row_ptr[r] * S >= c * nnz. */
+void oracle_sync_chunk_bounds(const int64_t *row_ptr, int32_t n, int32_t S, int32_t *bound)
+{
+    int64_t nnz = row_ptr[n];
+    bound[0] = 0;
+    bound[S] = n;
+    int32_t r = 0;
+    for (int32_t c = 1; c < S; ++c) {
+        while (r < n && row_ptr[r] * (int64_t)S < (int64_t)c * nnz)
+            ++r;
+        bound[c] = r;
+    }
+}
+
+/* Sum of all sampled forces of rows [r0, r1) with Y frozen, in CSR order,
+ * added into D (n x 2). */
+static void chunk_displacement(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                               const double *Y, int32_t r0, int32_t r1, int32_t k,
+                               uint32_t t, uint64_t seed, double *D)
+{
+    for (int32_t i = r0; i < r1; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            double fx, fy;
+            attraction_on_i(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                            Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1], &fx, &fy);
+            D[2 * (int64_t)i] += fx;
+            D[2 * (int64_t)i + 1] += fy;
+            D[2 * (int64_t)j] -= fx;
+            D[2 * (int64_t)j + 1] -= fy;
+            for (int32_t m = 0; m < k; ++m) {
+                int32_t s = oracle_uniform_negative(
+                    oracle_edge_word((uint64_t)e, t, (uint32_t)m, seed), i, n);
+                repulsion_on_i(Y[2 * (int64_t)i] - Y[2 * (int64_t)s],
+                               Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)s + 1], &fx, &fy);
+                D[2 * (int64_t)i] += fx;
+                D[2 * (int64_t)i + 1] += fy;
+                D[2 * (int64_t)s] -= fx;
+                D[2 * (int64_t)s + 1] -= fy;
+            }
+        }
+    }
+}
+
+/* One frozen-position epoch displacement (all rows, one chunk): the sampled
+ * estimate whose expectation Section 3.3 derives. */
+int oracle_epoch_displacement(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                              const double *Y, int32_t t, int32_t k, uint64_t seed, double *D)
+{
+    memset(D, 0, sizeof(double) * 2 * (size_t)n);
+    chunk_displacement(row_ptr, col_idx, n, Y, 0, n, k, (uint32_t)t, seed, D);
+    return 0;
+}
+
+/* Synchronous mode: per epoch, S chunks of rows; for each chunk the forces of
+ * its edges and negatives are summed from positions frozen at the chunk's
+ * start, then Y += eta_t * D.  With cap > 0 each node's step is clipped to
+ * length cap * eta_t / eta0.  Returns 0, or -1 on allocation failure. */
+int oracle_sync(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double *Y,
+                int32_t epoch_begin, int32_t epochs, int32_t k,
+                int32_t sched_kind, double eta0, double eta_min, int32_t total_epochs,
+                uint64_t seed, int32_t S, double cap)
+{
+    if (S < 1)
+        S = 1;
+    double *D = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    int32_t *bound = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S + 1));
+    if (!D || !bound) {
+        free(D);
+        free(bound);
+        return -1;
+    }
+    oracle_sync_chunk_bounds(row_ptr, n, S, bound);
+    for (int32_t ep = 0; ep < epochs; ++ep) {
+        int32_t t = epoch_begin + ep;
+        double eta = oracle_step_size(sched_kind, eta0, eta_min, total_epochs, t);
+        for (int32_t c = 0; c < S; ++c) {
+            memset(D, 0, sizeof(double) * 2 * (size_t)n);
+            chunk_displacement(row_ptr, col_idx, n, Y, bound[c], bound[c + 1], k, (uint32_t)t, seed, D);
+            double limit = cap * eta / eta0;
+            for (int32_t i = 0; i < n; ++i) {
+                double sx = eta * D[2 * (int64_t)i], sy = eta * D[2 * (int64_t)i + 1];
+                if (cap > 0.0) {
+                    double len = sqrt(sx * sx + sy * sy);
+                    if (len > limit) {
+                        sx *= limit / len;
+                        sy *= limit / len;
+                    }
+                }
+                Y[2 * (int64_t)i] += sx;
+                Y[2 * (int64_t)i + 1] += sy;
+            }
+        }
+    }
+    free(D);
+    free(bound);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Objective (Eq. 4) with the weight realised by uniform edge-centric       */
+/* sampling (Section 3.3): w_ij = (d_i+d_j) / (2(n-1)).                     */
+/* out = {attraction, repulsion, total, repulsion with Eq. 5's 2n weight}.  */
+/* ------------------------------------------------------------------------ */
+int oracle_objective(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                     const double *Y, int32_t k, double out[4])
+{
+    double attr = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            if (i < j)
+                attr += energy_attr(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                                    Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
+        }
+    double rep_num = 0.0;   /* sum over i<j of (d_i + d_j) U^r */
+    for (int32_t i = 0; i < n; ++i) {
+        double di = (double)(row_ptr[i + 1] - row_ptr[i]);
+        for (int32_t j = i + 1; j < n; ++j) {
+            double dj = (double)(row_ptr[j + 1] - row_ptr[j]);
+            rep_num += (di + dj) * energy_rep(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                                              Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
+        }
+    }
+    double rep = n > 1 ? (double)k * rep_num / (2.0 * (double)(n - 1)) : 0.0;
+    out[0] = attr;
+    out[1] = rep;
+    out[2] = attr + rep;
+    out[3] = n > 0 ? (double)k * rep_num / (2.0 * (double)n) : 0.0;
+    return 0;
+}
+
+/* Unbiased estimate of the same objective for large n: the attraction sum is
+ * exact; the pair sum is n(n-1)/2 times the mean over `pairs` uniform
+ * unordered pairs drawn from Philox(counter = (p_lo, p_hi, 0xFFFFFFFD, 0),
+ * key = seed).  out as in oracle_objective (out[3] left 0). */
+int oracle_objective_sampled(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                             const double *Y, int32_t k, int64_t pairs, uint64_t seed,
+                             double out[4])
+{
+    double attr = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            if (i < j)
+                attr += energy_attr(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                                    Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
+        }
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double acc = 0.0;
+    for (int64_t p = 0; p < pairs; ++p) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0xFFFFFFFDu, 0u};
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        int32_t i = (int32_t)(((uint64_t)w[0] * (uint64_t)(uint32_t)n) >> 32);
+        int32_t j = oracle_uniform_negative(w[1], i, n);
+        double di = (double)(row_ptr[i + 1] - row_ptr[i]);
+        double dj = (double)(row_ptr[j + 1] - row_ptr[j]);
+        acc += (di + dj) * energy_rep(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                                      Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
+    }
+    double npairs = 0.5 * (double)n * (double)(n - 1);
+    double rep = pairs > 0 && n > 1 ? (double)k * (acc / (double)pairs) * npairs / (2.0 * (double)(n - 1)) : 0.0;
+    out[0] = attr;
+    out[1] = rep;
+    out[2] = attr + rep;
+    out[3] = 0.0;
+    return 0;
+}
+
+/* Gradient of the objective above with respect to every y_i (n x 2). */
+int oracle_exact_gradient(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                          const double *Y, int32_t k, double *G)
+{
+    memset(G, 0, sizeof(double) * 2 * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            double fx, fy;
+            attraction_on_i(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                            Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1], &fx, &fy);
+            G[2 * (int64_t)i] -= fx;          /* grad = -force */
+            G[2 * (int64_t)i + 1] -= fy;
+        }
+    if (n < 2)
+        return 0;
+    double norm = (double)k / (2.0 * (double)(n - 1));
+    for (int32_t i = 0; i < n; ++i) {
+        double di = (double)(row_ptr[i + 1] - row_ptr[i]);
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double dj = (double)(row_ptr[j + 1] - row_ptr[j]);
+            double fx, fy;
+            repulsion_on_i(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                           Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1], &fx, &fy);
+            G[2 * (int64_t)i] -= norm * (di + dj) * fx;
+            G[2 * (int64_t)i + 1] -= norm * (di + dj) * fy;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbourhood preservation (Section 4.1, Metrics), r = 2:                */
+/*   NP = mean_i |N_G(i,2) & N_L(i,k_i)| / |N_G(i,2) | N_L(i,k_i)|,         */
+/* N_G(i,2) = nodes within two hops of i (i excluded), k_i = |N_G(i,2)|,    */
+/* N_L(i,k_i) = the k_i nodes nearest to y_i in the layout (i excluded),    */
+/* ties broken by the smaller node id.  Nodes with k_i = 0 are skipped.     */
+/* nodes == NULL evaluates every node, else the `count` listed ones.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double d2;
+    int32_t id;
+} np_item;
+
+static int np_less(const np_item *a, const np_item *b)
+{
+    return a->d2 < b->d2 || (a->d2 == b->d2 && a->id < b->id);
+}
+
+/* Rearrange v[0..len) so that its first kth items are the kth smallest. */
+static void np_select(np_item *v, int64_t len, int64_t kth)
+{
+    int64_t lo = 0, hi = len - 1;
+    uint64_t state = 0x9E3779B97F4A7C15ull;
+    while (lo < hi) {
+        state = state * 6364136223846793005ull + 1442695040888963407ull;
+        int64_t pidx = lo + (int64_t)((state >> 33) % (uint64_t)(hi - lo + 1));
+        np_item pivot = v[pidx];
+        int64_t a = lo, b = hi;
+        while (a <= b) {
+            while (np_less(&v[a], &pivot)) ++a;
+            while (np_less(&pivot, &v[b])) --b;
+            if (a <= b) {
+                np_item tmp = v[a]; v[a] = v[b]; v[b] = tmp;
+                ++a; --b;
+            }
+        }
+        if (kth - 1 <= b)
+            hi = b;
+        else if (kth - 1 >= a)
+            lo = a;
+        else
+            break;
+    }
+}
+
+double oracle_neighborhood_preservation(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                                        const double *Y, const int32_t *nodes, int32_t count)
+{
+    int32_t *stamp = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    np_item *items = (np_item *)malloc(sizeof(np_item) * (size_t)(n > 0 ? n : 1));
+    if (!stamp || !items) {
+        free(stamp);
+        free(items);
+        return -1.0;
+    }
+    int32_t total = nodes ? count : n;
+    double sum = 0.0;
+    int32_t used = 0;
+    for (int32_t q = 0; q < total; ++q) {
+        int32_t i = nodes ? nodes[q] : q;
+        int32_t mark = q + 1;
+        int64_t ki = 0;
+        stamp[i] = mark;   /* exclude i itself */
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            if (stamp[j] != mark) { stamp[j] = mark; ++ki; }
+        }
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            for (int64_t f = row_ptr[j]; f < row_ptr[j + 1]; ++f) {
+                int32_t l = col_idx[f];
+                if (stamp[l] != mark) { stamp[l] = mark; ++ki; }
+            }
+        }
+        if (ki == 0)
+            continue;
+        int64_t len = 0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double dx = Y[2 * (int64_t)i] - Y[2 * (int64_t)j];
+            double dy = Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1];
+            items[len].d2 = dx * dx + dy * dy;
+            items[len].id = j;
+            ++len;
+        }
+        np_select(items, len, ki);
+        int64_t inter = 0;
+        for (int64_t p = 0; p < ki; ++p)
+            if (stamp[items[p].id] == mark)
+                ++inter;
+        sum += (double)inter / (double)(2 * ki - inter);
+        ++used;
+        /* the stamp value of the next node differs, so no reset is needed */
+    }
+    free(stamp);
+    free(items);
+    return used > 0 ? sum / (double)used : 0.0;
+}
