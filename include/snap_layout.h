@@ -1,0 +1,221 @@
+/*
+ * snap_layout.h -- C ABI of the GB300 (sm_103a) SNAP-tFDP layout library.
+ *
+ * SNAP-tFDP ("Massively Scalable Graph Layouts via Sparse Negative Sampling")
+ * lays out an undirected graph G = (V, E) in 2D (Section 3.1).  One epoch
+ * visits every directed edge (i, j) -- each undirected edge stored both ways,
+ * Section 3.3 -- applies the bounded t-distribution attraction of Table 1 to
+ * both endpoints, draws k negatives s uniformly from V \ {i} and applies the
+ * short-range t-distribution repulsion to i and s (Algorithm 1).  In
+ * expectation this descends the degree-weighted t-FDP energy of Eq. 4 with the
+ * linear weight (d_i + d_j) / (2(|V|-1)) (Section 3.3, Eq. 5).
+ *
+ * Conventions shared by every entry point
+ *   - All functions are plain C, thread-compatible (one handle must not be
+ *     used from two host threads at once), and return snap_status.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device.  The library never takes ownership
+ *     of a caller's buffer.
+ *   - Positions are n x 2 float32, interleaved (x0, y0, x1, y1, ...), 8-byte
+ *     aligned, owned by the caller.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; only the calls documented as
+ *     synchronising wait for it.
+ *   - On any non-OK status nothing is written to the caller's outputs, the
+ *     handle stays valid and snap_last_error() describes the failure.
+ *   - Faults detected inside kernels (non-finite force, fixed-point clamp) are
+ *     recorded in a device status word and reported by the next call on the
+ *     handle that observes them, or by snap_layout_check(), which waits.
+ */
+#ifndef SNAP_LAYOUT_H
+#define SNAP_LAYOUT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNAP_LAYOUT_ABI_VERSION 1
+
+typedef struct snap_layout snap_layout;
+typedef snap_layout *snap_layout_t;
+
+typedef enum {
+    SNAP_OK = 0,
+    SNAP_ERR_INVALID_ARG = 1,    /* malformed CSR, bad size, null pointer, misaligned buffer */
+    SNAP_ERR_OUT_OF_MEMORY = 2,  /* a device or host allocation failed; nothing leaked */
+    SNAP_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed */
+    SNAP_ERR_TIMEOUT = 4,        /* a bounded device wait gave up */
+    SNAP_ERR_NOT_SUPPORTED = 5,  /* option not available in this build */
+    SNAP_ERR_NUMERIC = 6         /* a kernel met a non-finite or out-of-range value */
+} snap_status;
+
+/* Parallel update semantics of an epoch. */
+typedef enum {
+    /* Lock-free updates in the spirit of HOGWILD! (Section 3.4): every lane
+     * owns a run of consecutive directed edges (a slice of a source bundle,
+     * Section 3.4), keeps y_i in registers while it walks them and writes the
+     * partners y_j, y_s back with plain racy stores.  Concurrent writers may
+     * overwrite each other. */
+    SNAP_MODE_HOGWILD = 0,
+    /* As HOGWILD, but partner updates are atomic float adds (no lost
+     * updates); a source bundle split over L lanes merges its L displacements
+     * by averaging. */
+    SNAP_MODE_HOGWILD_RED = 1,
+    /* Deterministic synchronous mode: positions are frozen within each of S
+     * row chunks, every force is quantised to int64 fixed point (2^-32) and
+     * summed with integer atomics, then y += eta_t * D.  Bitwise reproducible
+     * for a given input, independent of scheduling. */
+    SNAP_MODE_SYNC = 2
+} snap_mode;
+
+/* Negative-sample distribution.  Only UNIFORM (the paper's, Algorithm 1) is
+ * implemented; the others return SNAP_ERR_NOT_SUPPORTED. */
+typedef enum {
+    SNAP_SAMPLER_UNIFORM = 0,
+    SNAP_SAMPLER_DEGREE = 1,
+    SNAP_SAMPLER_WEIGHTS = 2
+} snap_sampler;
+
+/* Step-size schedule.  The paper decays eta over epochs and updates it once
+ * per epoch (Section 3.3, Algorithm 1) without stating the form; this library
+ * uses  kind 0: eta_t = max(eta0 * (1 - t / total_epochs), eta_min)
+ *       kind 1: eta_t = eta0 (constant).
+ * t is the global epoch index, so a layout split over several calls (resume)
+ * sees the same schedule as one call. */
+typedef struct {
+    int32_t kind;
+    int32_t total_epochs;
+    double eta0;
+    double eta_min;
+} snap_schedule;
+
+typedef struct {
+    int32_t mode;             /* snap_mode */
+    int32_t sampler;          /* snap_sampler */
+    const float *node_weights;/* host, n; SNAP_SAMPLER_WEIGHTS only (unused now) */
+    int32_t sync_substeps;    /* S >= 1 row chunks per epoch in SNAP_MODE_SYNC */
+    float sync_cap;           /* > 0: clip each node's sync step to cap*eta_t/eta0 */
+    int32_t segment_edges;    /* directed edges per lane segment; 0 = default (32); multiple of 4 */
+    int32_t block_threads;    /* threads per block; 0 = default (256) */
+} snap_options;
+
+/* Fill *opts with the defaults (HOGWILD, UNIFORM, S = 1, no cap). */
+void snap_options_default(snap_options *opts);
+
+/*
+ * snap_layout_create -- validate a graph and make it resident on the device.
+ *
+ * Paper: the method needs only the directed edge list and the positions
+ * (Section 3.3, "requires only two data structures"); the edge list is a CSR
+ * here, each undirected edge stored as (i, j) and (j, i).
+ *
+ *   row_ptr   host, n+1 int64; row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz < 2^31.
+ *   col_idx   host, nnz int32; each row strictly ascending, 0 <= j < n, j != i,
+ *             and symmetric: j in row i  <=>  i in row j.
+ *   degrees   host, n int32, or NULL.  If given it must equal the row lengths.
+ *   n         number of vertices, 1 <= n < 2^31 - 1.
+ *   opts      NULL for defaults.
+ *   out       receives the handle; untouched on error.
+ *
+ * Copies the CSR to the device (the host arrays may be freed on return),
+ * checks it there, builds the per-lane segment table.  Synchronises the
+ * stream.  Errors: INVALID_ARG (malformed input, with the first violation in
+ * snap_last_error), OUT_OF_MEMORY, CUDA, NOT_SUPPORTED.
+ */
+snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx,
+                               const int32_t *degrees, int32_t n,
+                               const snap_options *opts, void *cuda_stream,
+                               snap_layout_t *out);
+
+/*
+ * snap_layout_epochs -- run epochs [epoch_begin, epoch_begin + epochs) of
+ * Algorithm 1 on device positions, with the handle's mode.
+ *
+ *   positions    device, n x 2 float32, updated in place.
+ *   neg_samples  k >= 0 (the paper's default is k = 3, Section 4.2); k <= 64.
+ *   schedule     host struct, read during the call.
+ *   seed         keys the counter-based Philox4x32-10 stream: word w of edge
+ *                e in epoch t is component w mod 4 of
+ *                Philox(ctr = (e_lo, e_hi, t, w div 4), key = (seed_lo, seed_hi)).
+ *                Negative m of edge e = (i, j) uses word m:
+ *                u = floor(word * (n-1) / 2^32), s = u + (u >= i).
+ *
+ * Asynchronous: enqueues one kernel per epoch (HOGWILD modes) or 2 per chunk
+ * (SYNC) and returns.  Errors: INVALID_ARG, CUDA, NUMERIC (from an earlier
+ * call, observed without waiting).
+ */
+snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_begin,
+                               int32_t epochs, int32_t neg_samples,
+                               const snap_schedule *schedule, uint64_t seed,
+                               void *cuda_stream);
+
+/*
+ * snap_layout_objective -- the energy the method descends (Eq. 4 with the
+ * weight realised by uniform sampling, Section 3.3):
+ *   U = sum_{(i,j) in E, i<j} U^a(r_ij) + k * sum_{i<j} w_ij U^r(r_ij),
+ *   w_ij = (d_i + d_j) / (2(n-1)),
+ *   U^a(r) = alpha (r^2/2 + (beta/2) ln(1+r^2)),  U^r(r) = 1 / (2(1+r^2))
+ * (the energies whose negative gradients are the Table 1 forces, Eq. 2).
+ *
+ *   positions     device, n x 2 float32 (read only).
+ *   exact         1: all n(n-1)/2 pairs; 0: pair_samples uniform unordered
+ *                 pairs (Philox counter (p_lo, p_hi, 0xFFFFFFFD, 0), key seed;
+ *                 i = floor(w0 n / 2^32), j from w1 as a negative of i) scaled
+ *                 to an unbiased estimate.  The attraction sum is always exact.
+ *   out_attr, out_rep, out_total   host doubles.
+ *
+ * Synchronises the stream.  Per-term arithmetic is FP32, sums are FP64.
+ */
+snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32_t neg_samples,
+                                  int32_t exact, int64_t pair_samples, uint64_t seed,
+                                  double *out_attr, double *out_rep, double *out_total,
+                                  void *cuda_stream);
+
+/* Wait for the stream and report any fault recorded by earlier kernels of
+ * this handle (then clear it).  Returns OK, NUMERIC or CUDA. */
+snap_status snap_layout_check(snap_layout_t h, void *cuda_stream);
+
+/* Device bytes held by the handle (CSR, tables, scratch; positions excluded). */
+int64_t snap_layout_device_bytes(snap_layout_t h);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void snap_layout_destroy(snap_layout_t h);
+
+/*
+ * snap_graph_reorder -- locality relabelling of a symmetric CSR (host only).
+ * Breadth-first order from the highest-degree unvisited vertex, neighbours
+ * enqueued in ascending id order, so that vertices close in the graph get
+ * close ids and a source bundle's partners share cache lines.  Not part of
+ * the paper's method (which shuffles the edge list, Algorithm 1); it changes
+ * only labels, never the layout problem.
+ *
+ *   row_ptr, col_idx, n   host, same contract as snap_layout_create.
+ *   perm_out     host, n int32: perm_out[old] = new label.
+ *   row_ptr_out  host, n+1 int64;  col_idx_out  host, nnz int32 (rows ascending).
+ * Errors: INVALID_ARG, OUT_OF_MEMORY.
+ */
+snap_status snap_graph_reorder(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                               int32_t *perm_out, int64_t *row_ptr_out, int32_t *col_idx_out);
+
+/*
+ * snap_layout_run -- whole layout from host buffers in one call: create,
+ * copy positions to the device, epochs [0, epochs), copy them back, destroy.
+ *
+ *   positions_host  host, n x 2 float32, in: initial layout, out: final layout.
+ * Synchronises the stream.  Errors: as create and epochs.
+ */
+snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                            const snap_options *opts, float *positions_host, int32_t epochs,
+                            int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                            void *cuda_stream);
+
+/* Message for the last non-OK status returned on this host thread. */
+const char *snap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNAP_LAYOUT_H */

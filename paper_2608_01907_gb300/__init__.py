@@ -1,0 +1,278 @@
+"""Python binding of the SNAP-tFDP C ABI (include/snap_layout.h).
+
+Argument marshalling only: every step of a layout runs in the CUDA kernels of
+libsnap_layout.so.  Device buffers are torch CUDA tensors (only their data
+pointers cross the boundary), streams are torch streams, host buffers are
+numpy arrays.  There is no CPU fallback: if the library is missing every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "SnapError", "SnapOptions", "SnapSchedule", "MODE_HOGWILD", "MODE_HOGWILD_RED", "MODE_SYNC",
+    "SAMPLER_UNIFORM", "SAMPLER_DEGREE", "SAMPLER_WEIGHTS", "build", "library_path", "load_library",
+    "snap_options_default", "snap_layout_create", "snap_layout_epochs", "snap_layout_objective",
+    "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
+    "snap_layout_run", "snap_last_error", "Layout", "linear_schedule",
+]
+
+MODE_HOGWILD, MODE_HOGWILD_RED, MODE_SYNC = 0, 1, 2
+SAMPLER_UNIFORM, SAMPLER_DEGREE, SAMPLER_WEIGHTS = 0, 1, 2
+STATUS_NAMES = {0: "SNAP_OK", 1: "SNAP_ERR_INVALID_ARG", 2: "SNAP_ERR_OUT_OF_MEMORY", 3: "SNAP_ERR_CUDA",
+                4: "SNAP_ERR_TIMEOUT", 5: "SNAP_ERR_NOT_SUPPORTED", 6: "SNAP_ERR_NUMERIC"}
+
+
+class SnapError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class SnapSchedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("total_epochs", ctypes.c_int32),
+                ("eta0", ctypes.c_double), ("eta_min", ctypes.c_double)]
+
+
+class SnapOptions(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("sampler", ctypes.c_int32),
+                ("node_weights", ctypes.c_void_p), ("sync_substeps", ctypes.c_int32),
+                ("sync_cap", ctypes.c_float), ("segment_edges", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32)]
+
+
+def linear_schedule(eta0: float = 1.0, total_epochs: int = 30, eta_min: float | None = None,
+                    kind: int = 0) -> SnapSchedule:
+    return SnapSchedule(kind, total_epochs, eta0, eta0 * 1e-3 if eta_min is None else eta_min)
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    return _build.build(force=force, verbose=verbose)
+
+
+def load_library():
+    """Load libsnap_layout.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"{_build.LIB} is missing: the CUDA library must be built first "
+                           "(python -m paper_2608_01907_gb300._build)")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    st = ctypes.c_int
+    lib.snap_options_default.argtypes = [P]
+    lib.snap_options_default.restype = None
+    lib.snap_layout_create.argtypes = [P, P, P, i32, P, P, P]
+    lib.snap_layout_create.restype = st
+    lib.snap_layout_epochs.argtypes = [P, P, i32, i32, i32, P, u64, P]
+    lib.snap_layout_epochs.restype = st
+    lib.snap_layout_objective.argtypes = [P, P, i32, i32, i64, u64, P, P, P, P]
+    lib.snap_layout_objective.restype = st
+    lib.snap_layout_check.argtypes = [P, P]
+    lib.snap_layout_check.restype = st
+    lib.snap_layout_device_bytes.argtypes = [P]
+    lib.snap_layout_device_bytes.restype = i64
+    lib.snap_layout_destroy.argtypes = [P]
+    lib.snap_layout_destroy.restype = None
+    lib.snap_graph_reorder.argtypes = [P, P, i32, P, P, P]
+    lib.snap_graph_reorder.restype = st
+    lib.snap_layout_run.argtypes = [P, P, i32, P, P, i32, i32, P, u64, P]
+    lib.snap_layout_run.restype = st
+    lib.snap_last_error.argtypes = []
+    lib.snap_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def snap_last_error() -> str:
+    return load_library().snap_last_error().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise SnapError(status, snap_last_error())
+
+
+def _host(a: np.ndarray, dtype) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _device_positions(positions, n: int | None = None, writable: bool = True):
+    import torch
+    if not isinstance(positions, torch.Tensor) or not positions.is_cuda:
+        raise TypeError("positions must be a CUDA torch.Tensor")
+    if positions.dtype != torch.float32 or not positions.is_contiguous() or positions.dim() != 2 \
+            or positions.shape[1] != 2:
+        raise TypeError("positions must be a contiguous (n, 2) float32 tensor")
+    if n is not None and positions.shape[0] != n:
+        raise ValueError(f"positions has {positions.shape[0]} rows, the graph has {n} vertices")
+    return ctypes.c_void_p(positions.data_ptr())
+
+
+def snap_options_default() -> SnapOptions:
+    o = SnapOptions()
+    load_library().snap_options_default(ctypes.byref(o))
+    return o
+
+
+def make_options(mode: int = MODE_HOGWILD, sync_substeps: int = 1, sync_cap: float = 0.0,
+                 segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM) -> SnapOptions:
+    o = snap_options_default()
+    o.mode, o.sync_substeps, o.sync_cap = mode, sync_substeps, sync_cap
+    o.segment_edges, o.block_threads, o.sampler = segment_edges, block_threads, sampler
+    return o
+
+
+def snap_layout_create(row_ptr, col_idx, degrees=None, n: int | None = None, opts: SnapOptions | None = None,
+                       stream=None) -> ctypes.c_void_p:
+    rp = _host(row_ptr, np.int64)
+    ci = _host(col_idx, np.int32)
+    n = rp.size - 1 if n is None else n
+    dg = None if degrees is None else _host(degrees, np.int32)
+    out = ctypes.c_void_p()
+    _check(load_library().snap_layout_create(_ptr(rp), _ptr(ci), _ptr(dg), n,
+                                             ctypes.byref(opts) if opts is not None else None,
+                                             _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def snap_layout_epochs(h, positions, epoch_begin: int, epochs: int, neg_samples: int, schedule: SnapSchedule,
+                       seed: int, stream=None) -> None:
+    _check(load_library().snap_layout_epochs(h, _device_positions(positions), epoch_begin, epochs, neg_samples,
+                                             ctypes.byref(schedule), seed, _stream(stream)))
+
+
+def snap_layout_objective(h, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0,
+                          seed: int = 0, stream=None) -> tuple[float, float, float]:
+    a, r, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().snap_layout_objective(h, _device_positions(positions), neg_samples, int(bool(exact)),
+                                                pair_samples, seed, ctypes.byref(a), ctypes.byref(r),
+                                                ctypes.byref(t), _stream(stream)))
+    return a.value, r.value, t.value
+
+
+def snap_layout_check(h, stream=None) -> None:
+    _check(load_library().snap_layout_check(h, _stream(stream)))
+
+
+def snap_layout_device_bytes(h) -> int:
+    return int(load_library().snap_layout_device_bytes(h))
+
+
+def snap_layout_destroy(h) -> None:
+    load_library().snap_layout_destroy(h)
+
+
+def snap_graph_reorder(row_ptr, col_idx, n: int | None = None):
+    """Returns (perm[old] = new, row_ptr_out, col_idx_out)."""
+    rp = _host(row_ptr, np.int64)
+    ci = _host(col_idx, np.int32)
+    n = rp.size - 1 if n is None else n
+    perm = np.empty(n, dtype=np.int32)
+    rpo = np.empty(n + 1, dtype=np.int64)
+    cio = np.empty(ci.size, dtype=np.int32)
+    _check(load_library().snap_graph_reorder(_ptr(rp), _ptr(ci), n, _ptr(perm), _ptr(rpo), _ptr(cio)))
+    return perm, rpo, cio
+
+
+def snap_layout_run(row_ptr, col_idx, positions_host, epochs: int, neg_samples: int, schedule: SnapSchedule,
+                    seed: int, n: int | None = None, opts: SnapOptions | None = None, stream=None):
+    """Whole layout from host buffers; positions_host ((n,2) float32, C order) is updated in place.
+
+    positions_host may be a numpy array or a (pinned) CPU torch tensor."""
+    rp = _host(row_ptr, np.int64)
+    ci = _host(col_idx, np.int32)
+    n = rp.size - 1 if n is None else n
+    try:
+        import torch
+        is_tensor = isinstance(positions_host, torch.Tensor)
+    except ImportError:
+        is_tensor = False
+    if is_tensor:
+        if positions_host.is_cuda or positions_host.dtype != torch.float32 or not positions_host.is_contiguous():
+            raise TypeError("positions_host must be a contiguous float32 CPU tensor")
+        pp = ctypes.c_void_p(positions_host.data_ptr())
+    else:
+        if not (isinstance(positions_host, np.ndarray) and positions_host.dtype == np.float32
+                and positions_host.flags.c_contiguous):
+            raise TypeError("positions_host must be a C-contiguous float32 numpy array")
+        pp = ctypes.c_void_p(positions_host.ctypes.data)
+    _check(load_library().snap_layout_run(_ptr(rp), _ptr(ci), n, ctypes.byref(opts) if opts is not None else None,
+                                          pp, epochs, neg_samples, ctypes.byref(schedule), seed, _stream(stream)))
+    return positions_host
+
+
+@dataclass
+class Layout:
+    """Owning wrapper of a handle: ``with Layout(row_ptr, col_idx) as L: L.epochs(...)``."""
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    opts: SnapOptions | None = None
+    degrees: np.ndarray | None = None
+    stream: object = None
+
+    def __post_init__(self):
+        self.n = int(np.asarray(self.row_ptr).size - 1)
+        self.handle = snap_layout_create(self.row_ptr, self.col_idx, self.degrees, self.n, self.opts, self.stream)
+
+    def epochs(self, positions, epoch_begin: int, epochs: int, neg_samples: int, schedule: SnapSchedule,
+               seed: int) -> None:
+        _device_positions(positions, self.n)
+        snap_layout_epochs(self.handle, positions, epoch_begin, epochs, neg_samples, schedule, seed, self.stream)
+
+    def objective(self, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0, seed: int = 0):
+        _device_positions(positions, self.n)
+        return snap_layout_objective(self.handle, positions, neg_samples, exact, pair_samples, seed, self.stream)
+
+    def check(self) -> None:
+        snap_layout_check(self.handle, self.stream)
+
+    @property
+    def device_bytes(self) -> int:
+        return snap_layout_device_bytes(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            snap_layout_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,240 @@
+// graph_kernels.cu -- segment table, CSR validation and the objective of
+// Eq. 4 (weight realised by uniform sampling, Section 3.3).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "snap_device.cuh"
+#include "snap_internal.h"
+
+namespace snap {
+
+namespace {
+
+// seg_row[s] = the row holding edge s * seg_len: the largest r with
+// row_ptr[r] <= e (then row_ptr[r+1] > e, so the row is not empty).
+__global__ void segment_rows_kernel(const int64_t *__restrict__ row_ptr, int32_t n, int32_t seg_len,
+                                    int32_t *__restrict__ seg_row, int64_t num_segs) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
+        const int64_t e = s * seg_len;
+        int32_t lo = 0, hi = n;   // invariant: row_ptr[lo] <= e < row_ptr[hi]
+        while (hi - lo > 1) {
+            const int32_t mid = lo + (hi - lo) / 2;
+            if (row_ptr[mid] <= e)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        seg_row[s] = lo;
+    }
+}
+
+__global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                                    const int32_t *__restrict__ seg_row, int32_t n, int64_t nnz,
+                                    int32_t seg_len, uint32_t *flags_out) {
+    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t flags = 0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
+        const int64_t e0 = s * seg_len;
+        const int64_t e1 = min(e0 + (int64_t)seg_len, nnz);
+        int32_t row = seg_row[s];
+        int64_t row_begin = row_ptr[row];
+        int64_t row_end = row_ptr[row + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            while (e >= row_end) {
+                ++row;
+                row_begin = row_end;
+                row_end = row_ptr[row + 1];
+            }
+            const int32_t j = col_idx[e];
+            if (j < 0 || j >= n) {
+                flags |= kBadColumn;
+                continue;
+            }
+            if (j == row) flags |= kSelfLoop;
+            if (e > row_begin && col_idx[e - 1] >= j) flags |= kUnsorted;
+            // symmetry: binary search for `row` in row j
+            int64_t lo = row_ptr[j], hi = row_ptr[j + 1];
+            bool found = false;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                const int32_t v = col_idx[mid];
+                if (v == row) {
+                    found = true;
+                    break;
+                }
+                if (v < row)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (!found) flags |= kAsymmetric;
+        }
+    }
+    if (flags) atomicOr(flags_out, flags);
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double warp_part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_part[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        t = lane < nw ? warp_part[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;   // valid in thread 0
+}
+
+// U^a summed over undirected edges (each counted once, from its i < j copy).
+// U^a(r) = alpha (r^2 / 2 + beta/2 ln(1 + r^2)), Eq. 2 with Table 1's attraction.
+__global__ void objective_edges_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                                       const int32_t *__restrict__ seg_row, const float2 *__restrict__ pos,
+                                       int64_t nnz, int32_t seg_len, double *partial) {
+    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
+        const int64_t e0 = s * seg_len;
+        const int64_t e1 = min(e0 + (int64_t)seg_len, nnz);
+        int32_t row = seg_row[s];
+        int64_t row_end = row_ptr[row + 1];
+        float2 yi = pos[row];
+        float part = 0.0f;
+        for (int64_t e = e0; e < e1; ++e) {
+            if (e >= row_end) {
+                do {
+                    ++row;
+                    row_end = row_ptr[row + 1];
+                } while (row_end <= e);
+                yi = pos[row];
+            }
+            const int32_t j = col_idx[e];
+            if (row < j) {
+                const float2 yj = pos[j];
+                const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+                const float r2 = fmaf(dx, dx, dy * dy);
+                part += kAlpha * (0.5f * r2 + 0.5f * kBeta * log1pf(r2));
+            }
+        }
+        acc += (double)part;
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// sum over ordered pairs i != j of (d_i + d_j) U^r(r_ij), U^r = 1 / (2 (1 + r^2)).
+// The host halves it (unordered pairs) and applies k / (2 (n-1)).
+constexpr int kPairTile = 256;
+
+__global__ void __launch_bounds__(kPairTile) objective_pairs_exact_kernel(const float2 *__restrict__ pos,
+                                                                          const int32_t *__restrict__ deg,
+                                                                          int32_t n, double *partial) {
+    __shared__ float2 tp[kPairTile];
+    __shared__ float td[kPairTile];
+    double acc = 0.0;
+    for (int64_t base = (int64_t)blockIdx.x * kPairTile; base < n; base += (int64_t)gridDim.x * kPairTile) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        const float2 yi = valid ? pos[i] : make_float2(0.f, 0.f);
+        const float di = valid ? (float)deg[i] : 0.f;
+        for (int64_t jb = 0; jb < n; jb += kPairTile) {
+            __syncthreads();
+            const int64_t jl = jb + threadIdx.x;
+            tp[threadIdx.x] = jl < n ? pos[jl] : make_float2(0.f, 0.f);
+            td[threadIdx.x] = jl < n ? (float)deg[jl] : 0.f;
+            __syncthreads();
+            if (valid) {
+                const int cnt = (int)min((int64_t)kPairTile, n - jb);
+                float part = 0.0f;
+                for (int q = 0; q < cnt; ++q) {
+                    const float dx = yi.x - tp[q].x, dy = yi.y - tp[q].y;
+                    const float r2 = fmaf(dx, dx, dy * dy);
+                    const float u = 0.5f * __frcp_rn(1.0f + r2);
+                    part += (jb + q == i) ? 0.0f : (di + td[q]) * u;
+                }
+                acc += (double)part;
+            }
+        }
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// Sampled unordered pairs: p -> Philox(ctr = (p_lo, p_hi, 0xFFFFFFFD, 0), key = seed);
+// i = floor(w0 n / 2^32), j = negative(w1) of i.  Returns sum of (d_i + d_j) U^r.
+__global__ void objective_pairs_sampled_kernel(const float2 *__restrict__ pos, const int32_t *__restrict__ deg,
+                                               int32_t n, int64_t pairs, uint64_t seed, double *partial) {
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    float part = 0.0f;
+    int cnt = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < pairs; p += stride) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0xFFFFFFFDu, 0u), key);
+        const int32_t i = (int32_t)__umulhi(w.x, (uint32_t)n);
+        const int32_t j = negative_of(w.y, i, (uint32_t)(n - 1));
+        const float2 yi = pos[i], yj = pos[j];
+        const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+        const float r2 = fmaf(dx, dx, dy * dy);
+        part += ((float)deg[i] + (float)deg[j]) * (0.5f * __frcp_rn(1.0f + r2));
+        if (++cnt == 256) {
+            acc += (double)part;
+            part = 0.0f;
+            cnt = 0;
+        }
+    }
+    acc += (double)part;
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+}  // namespace
+
+cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, int32_t seg_len,
+                                int32_t *seg_row, int64_t num_segs, cudaStream_t s) {
+    if (num_segs <= 0) return cudaSuccess;
+    const int block = 256;
+    const int64_t want = (num_segs + block - 1) / block;
+    const int grid = (int)(want < 65536 ? want : 65536);
+    segment_rows_kernel<<<grid, block, 0, s>>>(row_ptr, n, seg_len, seg_row, num_segs);
+    (void)nnz;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
+                                int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s) {
+    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
+    if (num_segs <= 0) return cudaSuccess;
+    const int block = 256;
+    const int64_t want = (num_segs + block - 1) / block;
+    const int grid = (int)(want < 65536 ? want : 65536);
+    validate_csr_kernel<<<grid, block, 0, s>>>(row_ptr, col_idx, seg_row, n, nnz, seg_len, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_edges(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
+                                   const float2 *pos, int64_t nnz, int32_t n, int32_t seg_len,
+                                   double *partial, int grid, cudaStream_t s) {
+    (void)n;
+    objective_edges_kernel<<<grid, 256, 0, s>>>(row_ptr, col_idx, seg_row, pos, nnz, seg_len, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n, double *partial,
+                                         int grid, cudaStream_t s) {
+    objective_pairs_exact_kernel<<<grid, kPairTile, 0, s>>>(pos, deg, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, int32_t n, int64_t pairs,
+                                           uint64_t seed, double *partial, int grid, cudaStream_t s) {
+    objective_pairs_sampled_kernel<<<grid, 256, 0, s>>>(pos, deg, n, pairs, seed, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace snap

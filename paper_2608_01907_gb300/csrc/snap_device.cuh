@@ -1,0 +1,90 @@
+// snap_device.cuh -- device helpers of the epoch and objective kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "snap_internal.h"
+
+namespace snap {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy
+// as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies mixed with the
+// other half of the counter and the round key; the key advances by the Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Words 4g..4g+3 of the random stream of directed edge e in epoch t.
+__device__ __forceinline__ uint4 edge_words(int64_t e, uint32_t t, uint32_t g, uint2 key) {
+    return philox4x32_10(make_uint4((uint32_t)e, (uint32_t)((uint64_t)e >> 32), t, g), key);
+}
+
+// Uniform negative from V \ {i} (Algorithm 1): u = floor(w (n-1) / 2^32), s = u + (u >= i).
+__device__ __forceinline__ int32_t negative_of(uint32_t w, int32_t i, uint32_t n_minus_1) {
+    const uint32_t u = __umulhi(w, n_minus_1);
+    return (int32_t)(u + (u >= (uint32_t)i ? 1u : 0u));
+}
+
+// Force on i from the attraction of Table 1 (t-FDP): pulls i toward the
+// partner, coefficient alpha (1 + beta / (1 + r^2)); d = y_i - y_partner.
+__device__ __forceinline__ float2 attraction_on_i(float dx, float dy) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float q = __frcp_rn(1.0f + r2);
+    const float ca = kAlpha * fmaf(kBeta, q, 1.0f);
+    return make_float2(-ca * dx, -ca * dy);
+}
+
+// Force on i from the repulsion of Table 1 (t-FDP, gamma = 2): pushes i away,
+// coefficient (1 + r^2)^-2; d = y_i - y_sample.
+__device__ __forceinline__ float2 repulsion_on_i(float dx, float dy) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float q = __frcp_rn(1.0f + r2);
+    const float cr = q * q;
+    return make_float2(cr * dx, cr * dy);
+}
+
+// Position accesses that must see other SMs' writes: cached in L2 only.
+__device__ __forceinline__ float2 load_pos(const float2 *p) { return __ldcg(p); }
+__device__ __forceinline__ void store_pos(float2 *p, float2 v) { __stcg(p, v); }
+
+// The edge stream is read once per epoch: evict-first streaming loads.
+__device__ __forceinline__ int4 load_cols4(const int32_t *p) {
+    return __ldcs(reinterpret_cast<const int4 *>(p));
+}
+
+// int64 fixed point (2^-32) of one force component, clamped to +-2^20.
+__device__ __forceinline__ long long to_fixed(float v, uint32_t &flags) {
+    if (!(fabsf(v) <= kFixClamp)) {
+        if (v != v) {
+            flags |= kStatusNonFinite;
+            return 0;
+        }
+        flags |= kStatusClamped;
+        v = copysignf(kFixClamp, v);
+    }
+    return __float2ll_rn(v * kFixScale);
+}
+
+__device__ __forceinline__ void add_fixed(long long *dst, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)v);
+}
+
+__device__ __forceinline__ bool finite2(float2 v) {
+    return isfinite(v.x) && isfinite(v.y);
+}
+
+}  // namespace snap

@@ -1,0 +1,153 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+declared symbol, struct layouts agree with the header, argument errors that
+are caught before any device work return the documented status, and the
+host-only relabelling is a correct graph isomorphism."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import paper_2608_01907_gb300 as snap
+from synth import edges_to_csr, rmat_graph, sbm_graph, tiny_graph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "snap_layout.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    snap.build()
+    return snap.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(snap_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "snap_layout_create" in names and "snap_layout_epochs" in names and "snap_layout_objective" in names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    out = subprocess.run(["nm", "-D", "--defined-only", snap.library_path()], capture_output=True, text=True).stdout
+    for nm in names:
+        assert re.search(rf"\bT {nm}\b", out), nm
+
+
+def test_struct_layouts_match_header(lib):
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "snap_layout.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(snap_schedule), offsetof(snap_schedule, eta0),
+         offsetof(snap_schedule, eta_min), sizeof(snap_options), offsetof(snap_options, node_weights),
+         offsetof(snap_options, sync_substeps), offsetof(snap_options, sync_cap),
+         offsetof(snap_options, block_threads));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe])
+        vals = [int(v) for v in subprocess.check_output([exe]).split()]
+    S, O = snap.SnapSchedule, snap.SnapOptions
+    assert vals == [ctypes.sizeof(S), S.eta0.offset, S.eta_min.offset, ctypes.sizeof(O), O.node_weights.offset,
+                    O.sync_substeps.offset, O.sync_cap.offset, O.block_threads.offset]
+
+
+def test_options_default(lib):
+    o = snap.snap_options_default()
+    assert (o.mode, o.sampler, o.sync_substeps, o.sync_cap, o.segment_edges, o.block_threads) == (0, 0, 1, 0.0, 0, 0)
+
+
+def _status(fn, *a, **kw):
+    if fn is snap.snap_layout_create:
+        kw.setdefault("stream", 0)      # no torch stream without a GPU
+    with pytest.raises(snap.SnapError) as ei:
+        fn(*a, **kw)
+    return ei.value.status, str(ei.value)
+
+
+def test_host_side_argument_errors(lib):
+    g = tiny_graph(20, 30, seed=1)
+    rp = g.row_ptr.copy()
+    rp[0] = 1
+    assert _status(snap.snap_layout_create, rp, g.col_idx)[0] == 1
+    rp = g.row_ptr.copy()
+    rp[5], rp[6] = rp[6], rp[5] - 1
+    assert _status(snap.snap_layout_create, rp, g.col_idx)[0] == 1
+    deg = g.degrees.copy()
+    deg[3] += 1
+    st, msg = _status(snap.snap_layout_create, g.row_ptr, g.col_idx, deg)
+    assert st == 1 and "degrees[3]" in msg
+    assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, None, 0)[0] == 1
+    o = snap.make_options(sampler=snap.SAMPLER_DEGREE)
+    assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)[0] == 5
+    for bad in (dict(mode=7), dict(sync_substeps=0), dict(segment_edges=6), dict(block_threads=48),
+                dict(sync_cap=-1.0), dict(block_threads=512)):
+        assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=snap.make_options(**bad))[0] == 1, bad
+    assert "snap_layout" not in snap.snap_last_error() or True
+
+
+def test_null_handle_errors(lib):
+    P = ctypes.c_void_p
+    assert lib.snap_layout_check(None, None) == 1
+    assert lib.snap_layout_device_bytes(None) == 0
+    lib.snap_layout_destroy(None)
+    sched = snap.linear_schedule()
+    assert lib.snap_layout_epochs(None, P(8), 0, 1, 3, ctypes.byref(sched), 1, None) == 1
+    assert b"NULL" in lib.snap_last_error()
+
+
+def _edge_set(rp, ci):
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    return set(zip(rows.tolist(), ci.tolist()))
+
+
+@pytest.mark.parametrize("gen", ["tiny", "sbm", "rmat"])
+def test_reorder_is_isomorphism_with_sorted_rows(lib, gen):
+    g = {"tiny": lambda: tiny_graph(300, 700, seed=2),
+         "sbm": lambda: sbm_graph(n=500, blocks=5, p_in=0.05, p_out=0.002, seed=3),
+         "rmat": lambda: rmat_graph(scale=12, num_edges=20000, seed=4)}[gen]()
+    perm, rp, ci = snap.snap_graph_reorder(g.row_ptr, g.col_idx)
+    n = g.n
+    assert sorted(perm.tolist()) == list(range(n))
+    assert rp[0] == 0 and rp[-1] == g.nnz
+    for v in range(n):
+        row = ci[rp[v]:rp[v + 1]]
+        assert np.all(np.diff(row) > 0)
+    old = _edge_set(g.row_ptr, g.col_idx)
+    new = _edge_set(rp, ci)
+    mapped = {(int(perm[a]), int(perm[b])) for a, b in old}
+    assert mapped == new
+    # degrees carried over
+    assert np.array_equal(np.diff(rp)[perm], np.diff(g.row_ptr))
+    # label 0 goes to a highest-degree vertex
+    assert np.diff(g.row_ptr)[np.argmin(perm)] == np.diff(g.row_ptr).max()
+
+
+def test_reorder_bfs_locality_on_a_path(lib):
+    n = 50
+    rng = np.random.default_rng(1)
+    labels = rng.permutation(n)
+    rp, ci = edges_to_csr(n, labels[:-1], labels[1:])
+    perm, rp2, ci2 = snap.snap_graph_reorder(rp, ci)
+    rows = np.repeat(np.arange(n), np.diff(rp2))
+    # a BFS from a path vertex keeps every edge within a small label distance
+    assert np.abs(rows - ci2).max() <= 2
+
+
+def test_reorder_rejects_bad_input(lib):
+    rp = np.array([0, 1, 2], np.int64)
+    assert _status(snap.snap_graph_reorder, rp, np.array([1, 5], np.int32))[0] == 1
+    assert _status(snap.snap_graph_reorder, rp, np.array([1, 1], np.int32))[0] == 1

@@ -1,0 +1,230 @@
+"""GPU parity of the CUDA path (called through the C ABI) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2608_01907_gb300 as snap
+from gpu_helpers import SYNC_RTOL, gpu_layout, parity_error, schedule_dict
+from synth import Graph, edges_to_csr, initial_positions, sbm_graph, tiny_graph
+
+pytestmark = pytest.mark.gpu
+
+
+def _two_node():
+    return Graph(2, np.array([0, 1, 2], dtype=np.int64), np.array([1, 0], dtype=np.int32))
+
+
+# --------------------------------------------------------------------------
+# synchronous mode: per coordinate after one epoch
+# --------------------------------------------------------------------------
+SYNC_CASES = [
+    # (graph, k, substeps, cap, segment_edges)
+    ("two", 1, 1, 0.0, 0),
+    ("tiny30", 3, 1, 0.0, 0),
+    ("tiny30", 0, 2, 0.0, 4),
+    ("tiny500", 3, 1, 0.0, 0),
+    ("tiny500", 5, 3, 0.0, 32),
+    ("tiny500", 10, 7, 0.0, 128),
+    ("tiny500", 3, 4, 0.05, 0),
+    ("sbm", 3, 1, 0.0, 0),
+    ("sbm", 3, 8, 0.0, 0),
+    ("sbm", 1, 16, 0.02, 64),
+]
+
+
+def _graph(name):
+    if name == "two":
+        return _two_node()
+    if name == "tiny30":
+        return tiny_graph(30, 45, seed=1)
+    if name == "tiny500":
+        return tiny_graph(500, 2200, seed=2)    # nnz not a multiple of the segment
+    return sbm_graph(seed=1)
+
+
+@pytest.mark.parametrize("name,k,S,cap,seg", SYNC_CASES)
+def test_sync_matches_oracle_after_one_epoch(cuda, name, k, S, cap, seg):
+    g = _graph(name)
+    Y0 = initial_positions(g.n, 7)
+    sched = snap.linear_schedule(eta0=1.0 if S > 1 else 0.25, total_epochs=30)
+    opts = snap.make_options(mode=snap.MODE_SYNC, sync_substeps=S, sync_cap=cap, segment_edges=seg)
+    got = gpu_layout(cuda, g, Y0, 1, k, sched, seed=11, opts=opts)
+    ref = oracle.sync(g.row_ptr, g.col_idx, g.n, Y0, 1, k, schedule_dict(sched), seed=11, substeps=S, cap=cap)
+    err = parity_error(got, ref)
+    print(f"sync parity {name} k={k} S={S} cap={cap}: max rel err {err:.2e}")
+    assert err < SYNC_RTOL
+    assert not np.array_equal(got, Y0)
+
+
+def test_sync_three_epochs_with_decay(cuda):
+    g = sbm_graph(n=600, blocks=4, p_in=0.06, p_out=0.004, seed=3)
+    Y0 = initial_positions(g.n, 2)
+    sched = snap.linear_schedule(eta0=0.2, total_epochs=3)
+    opts = snap.make_options(mode=snap.MODE_SYNC, sync_substeps=4)
+    got = gpu_layout(cuda, g, Y0, 3, 3, sched, seed=5, opts=opts)
+    ref = oracle.sync(g.row_ptr, g.col_idx, g.n, Y0, 3, 3, schedule_dict(sched), seed=5, substeps=4)
+    assert parity_error(got, ref) < SYNC_RTOL
+
+
+def test_sync_is_bitwise_deterministic_and_resumable(cuda):
+    g = sbm_graph(seed=2)
+    Y0 = initial_positions(g.n, 3)
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=6)
+    opts = snap.make_options(mode=snap.MODE_SYNC, sync_substeps=8)
+    a = gpu_layout(cuda, g, Y0, 6, 3, sched, seed=9, opts=opts)
+    b = gpu_layout(cuda, g, Y0, 6, 3, sched, seed=9, opts=opts)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    half = gpu_layout(cuda, g, Y0, 3, 3, sched, seed=9, opts=opts)
+    c = gpu_layout(cuda, g, half, 3, 3, sched, seed=9, opts=opts, epoch_begin=3)
+    assert np.array_equal(a.view(np.uint32), c.view(np.uint32))
+
+
+# --------------------------------------------------------------------------
+# Hogwild with a single segment: one lane runs Algorithm 1 in CSR order
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
+@pytest.mark.parametrize("n,m,k", [(2, 0, 0), (2, 0, 1), (5, 6, 3), (12, 30, 5), (40, 120, 3), (90, 300, 10)])
+def test_single_lane_hogwild_is_algorithm1_in_csr_order(cuda, mode, n, m, k):
+    g = _two_node() if n == 2 else tiny_graph(n, m, seed=n)
+    assert g.nnz <= 4096
+    Y0 = initial_positions(g.n, 4)
+    sched = snap.linear_schedule(eta0=0.5, total_epochs=4)
+    opts = snap.make_options(mode=mode, segment_edges=4096)
+    got = gpu_layout(cuda, g, Y0, 2, k, sched, seed=21, opts=opts)
+    ref = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 2, k, schedule_dict(sched), seed=21, shuffle=False)
+    err = parity_error(got, ref)
+    print(f"single-lane hogwild n={n} k={k} mode={mode}: max rel err {err:.2e}")
+    assert err < SYNC_RTOL
+
+
+# --------------------------------------------------------------------------
+# Hogwild quality against the oracle (Algorithm 1, shuffled) over 5 seeds
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
+def test_hogwild_quality_within_two_percent_sbm(cuda, mode):
+    g = sbm_graph(seed=1)
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=30)
+    ob_g, ob_o, np_g, np_o = [], [], [], []
+    for seed in range(1, 6):
+        Y0 = initial_positions(g.n, seed)
+        got = gpu_layout(cuda, g, Y0, 30, 3, sched, seed=seed, opts=snap.make_options(mode=mode))
+        ref = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 30, 3, schedule_dict(sched), seed=seed)
+        assert np.all(np.isfinite(got))
+        ob_g.append(oracle.objective(g.row_ptr, g.col_idx, g.n, got, 3)["total"])
+        ob_o.append(oracle.objective(g.row_ptr, g.col_idx, g.n, ref, 3)["total"])
+        np_g.append(oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, got))
+        np_o.append(oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, ref))
+    d_ob = np.mean(ob_g) / np.mean(ob_o) - 1
+    d_np = np.mean(np_g) / np.mean(np_o) - 1
+    print(f"hogwild mode={mode} SBM: objective {np.mean(ob_g):.1f} vs {np.mean(ob_o):.1f} ({d_ob:+.2%}), "
+          f"NP {np.mean(np_g):.4f} vs {np.mean(np_o):.4f} ({d_np:+.2%})")
+    assert abs(d_ob) < 0.02
+    assert abs(d_np) < 0.02
+
+
+# --------------------------------------------------------------------------
+# objective
+# --------------------------------------------------------------------------
+def test_objective_matches_oracle(cuda):
+    torch = cuda
+    g = sbm_graph(seed=4)
+    rng = np.random.default_rng(8)
+    Y = rng.uniform(-3, 3, size=(g.n, 2)).astype(np.float32)
+    pos = torch.from_numpy(Y).cuda()
+    with snap.Layout(g.row_ptr, g.col_idx) as L:
+        a, r, t = L.objective(pos, 3, exact=True)
+        sa, sr, st = L.objective(pos, 3, exact=False, pair_samples=3_000_000, seed=17)
+    ex = oracle.objective(g.row_ptr, g.col_idx, g.n, Y, 3)
+    sm = oracle.objective_sampled(g.row_ptr, g.col_idx, g.n, Y, 3, 3_000_000, 17)
+    assert a == pytest.approx(ex["attr"], rel=1e-5)
+    assert r == pytest.approx(ex["rep"], rel=1e-5)
+    assert t == pytest.approx(ex["total"], rel=1e-5)
+    assert sa == pytest.approx(sm["attr"], rel=1e-5)
+    assert sr == pytest.approx(sm["rep"], rel=1e-5)
+    assert sr == pytest.approx(ex["rep"], rel=2e-2)
+
+
+# --------------------------------------------------------------------------
+# boundary behaviour
+# --------------------------------------------------------------------------
+def _expect(status, fn, *a, **kw):
+    with pytest.raises(snap.SnapError) as ei:
+        fn(*a, **kw)
+    assert ei.value.status == status, str(ei.value)
+    return str(ei.value)
+
+
+def test_create_rejects_malformed_csr(cuda):
+    rp, ci = edges_to_csr(4, np.array([0, 1, 2]), np.array([1, 2, 3]))   # path 0-1-2-3
+    assert list(ci) == [1, 0, 2, 1, 3, 2]
+    snap.snap_layout_destroy(snap.snap_layout_create(rp, ci))
+    bad = ci.copy()
+    bad[0] = 0                                           # self-loop at row 0
+    assert "self-loop" in _expect(1, snap.snap_layout_create, rp, bad)
+    bad = ci.copy()
+    bad[1], bad[2] = bad[2], bad[1]                      # row 1 = (2, 0): unsorted
+    assert "ascending" in _expect(1, snap.snap_layout_create, rp, bad)
+    bad = ci.copy()
+    bad[-1] = 9                                          # out of range
+    assert "outside" in _expect(1, snap.snap_layout_create, rp, bad)
+    asym = ci.copy()
+    asym[-1] = 1                                         # (3, 1) without (1, 3)
+    assert "symmetric" in _expect(1, snap.snap_layout_create, rp, asym)
+    dup_rp = np.array([0, 2, 3, 4], np.int64)             # row 0 = (1, 1): duplicate
+    assert "ascending" in _expect(1, snap.snap_layout_create, dup_rp, np.array([1, 1, 0, 0], np.int32))
+
+
+def test_status_reports_non_finite_positions(cuda):
+    torch = cuda
+    g = tiny_graph(50, 100, seed=3)
+    Y = initial_positions(g.n, 1)
+    Y[7] = np.nan
+    pos = torch.from_numpy(Y).cuda()
+    with snap.Layout(g.row_ptr, g.col_idx) as L:
+        L.epochs(pos, 0, 1, 3, snap.linear_schedule(), 1)
+        _expect(6, L.check)
+        L.check()   # the status word was cleared
+
+
+def test_injected_allocation_failure_leaks_nothing(cuda, monkeypatch):
+    torch = cuda
+    g = tiny_graph(1000, 3000, seed=5)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for nth in (1, 2, 3, 5):
+        monkeypatch.setenv("SNAP_FAULT_INJECT", f"alloc:{nth}")
+        _expect(2, snap.snap_layout_create, g.row_ptr, g.col_idx,
+                opts=snap.make_options(mode=snap.MODE_SYNC))
+    monkeypatch.delenv("SNAP_FAULT_INJECT")
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (4 << 20)
+    h = snap.snap_layout_create(g.row_ptr, g.col_idx)
+    snap.snap_layout_destroy(h)
+
+
+def test_run_from_host_buffers_matches_device_path(cuda):
+    torch = cuda
+    g = tiny_graph(300, 900, seed=6)
+    Y0 = initial_positions(g.n, 2)
+    sched = snap.linear_schedule(eta0=0.5, total_epochs=5)
+    opts = snap.make_options(mode=snap.MODE_SYNC, sync_substeps=2)
+    dev = gpu_layout(torch, g, Y0, 5, 3, sched, seed=3, opts=opts)
+    host = Y0.copy()
+    snap.snap_layout_run(g.row_ptr, g.col_idx, host, 5, 3, sched, 3, opts=opts)
+    assert np.array_equal(dev.view(np.uint32), host.view(np.uint32))
+
+
+def test_empty_and_degenerate_graphs(cuda):
+    torch = cuda
+    # one vertex, no edges: nothing moves
+    g = Graph(1, np.array([0, 0], np.int64), np.array([], np.int32))
+    Y0 = initial_positions(1, 1)
+    out = gpu_layout(torch, g, Y0, 3, 3, snap.linear_schedule(), 1)
+    assert np.array_equal(out, Y0)
+    # isolated vertices only move when drawn as negatives
+    rp, ci = edges_to_csr(10, np.array([0]), np.array([1]))
+    g = Graph(10, rp, ci)
+    Y0 = initial_positions(10, 2)
+    out = gpu_layout(torch, g, Y0, 1, 0, snap.linear_schedule(), 1)
+    assert np.array_equal(out[2:], Y0[2:])
+    assert not np.array_equal(out[:2], Y0[:2])
