@@ -68,7 +68,7 @@ def _load():
     lib.oracle_step_size.restype = f64
     lib.oracle_pair_terms.argtypes = [f64, f64, P]
     lib.oracle_pair_terms.restype = None
-    lib.oracle_seq.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, u64, i64, P]
+    lib.oracle_seq.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, u64, i64, P, P]
     lib.oracle_seq.restype = ctypes.c_int
     lib.oracle_sync_chunk_bounds.argtypes = [P, i32, i32, P]
     lib.oracle_sync_chunk_bounds.restype = None
@@ -141,18 +141,24 @@ def pair_terms(dx: float, dy: float) -> np.ndarray:
 
 
 def seq(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, shuffle_seed=None,
-        epoch_begin=0, max_edges_per_epoch=-1, return_energy=False, shuffle=True):
+        epoch_begin=0, max_edges_per_epoch=-1, return_energy=False, shuffle=True, order=None):
     """Algorithm 1 (sequential, immediate updates).  Returns the final (n,2) float64.
 
-    shuffle=False visits the directed edges in CSR order."""
+    shuffle=False visits the directed edges in CSR order; `order` (a
+    permutation of the CSR edge indices) fixes the visiting order."""
     rp, ci = _csr(row_ptr, col_idx)
     Y = _positions(Y0).copy()
     kind, eta0, eta_min, total = _sched(schedule)
     en = np.zeros(max(epochs, 1))
     shuffle_seed = seed ^ 0x5DEECE66D if shuffle_seed is None else shuffle_seed
+    od = None
+    if order is not None:
+        od = np.ascontiguousarray(order, dtype=np.int64)
+        if od.size != rp[-1] or not np.array_equal(np.sort(od), np.arange(rp[-1])):
+            raise ValueError("order must be a permutation of the CSR edge indices")
     rc = _load().oracle_seq(_p(rp), _p(ci), n, _p(Y), epoch_begin, epochs, k, kind, eta0, eta_min,
                             total, seed, int(bool(shuffle)), shuffle_seed, max_edges_per_epoch,
-                            _p(en) if return_energy else None)
+                            _p(en) if return_energy else None, _p(od) if od is not None else None)
     if rc != 0:
         raise MemoryError("oracle_seq failed to allocate")
     return (Y, en[:epochs]) if return_energy else Y

@@ -183,7 +183,9 @@ static int32_t *row_of_edges(const int64_t *row_ptr, int32_t n)
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1, sequential, immediate updates.                              */
 /* Y is n x 2 row-major doubles, updated in place.  shuffle = 0 keeps the   */
-/* CSR order (one of the orders a shuffle can produce).                     */
+/* CSR order; given_order (nullable, a permutation of the nnz CSR indices)  */
+/* fixes the visiting order instead -- each is one of the orders the        */
+/* shuffle of Algorithm 1 can produce.                                      */
 /* max_edges_per_epoch < 0 processes every edge; otherwise only that many   */
 /* edges of the shuffled order are visited in each epoch (a timing sample). */
 /* actual_energy (nullable, one value per epoch): half the sum of U^a over  */
@@ -195,7 +197,7 @@ int oracle_seq(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double
                int32_t epoch_begin, int32_t epochs, int32_t k,
                int32_t sched_kind, double eta0, double eta_min, int32_t total_epochs,
                uint64_t seed, int32_t shuffle, uint64_t shuffle_seed, int64_t max_edges_per_epoch,
-               double *actual_energy)
+               double *actual_energy, const int64_t *given_order)
 {
     int64_t nnz = row_ptr[n];
     int32_t *src = row_of_edges(row_ptr, n);
@@ -208,7 +210,9 @@ int oracle_seq(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double
     /* "Randomly shuffle edge list E" -- once, before the epoch loop
      * (Fisher-Yates, driven by its own Philox stream). */
     for (int64_t e = 0; e < nnz; ++e)
-        order[e] = e;
+        order[e] = given_order ? given_order[e] : e;
+    if (given_order)
+        shuffle = 0;
     uint32_t skey[2] = {(uint32_t)shuffle_seed, (uint32_t)(shuffle_seed >> 32)};
     for (int64_t p = shuffle ? nnz - 1 : 0; p > 0; --p) {
         uint32_t ctr[4] = {(uint32_t)p, (uint32_t)((uint64_t)p >> 32), 0xFFFFFFFEu, 0u};

@@ -269,6 +269,22 @@ def test_seq_split_calls_equal_one_call():
     assert np.array_equal(full, half)
 
 
+def test_seq_explicit_order():
+    g = tiny_graph(40, 90, seed=12)
+    Y0 = initial_positions(g.n, 5)
+    sched = dict(eta0=0.7, total_epochs=3)
+    csr = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 3, 3, sched, seed=2, shuffle=False)
+    same = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 3, 3, sched, seed=2, order=np.arange(g.nnz))
+    assert np.array_equal(csr, same)
+    # any visiting order keeps every update of the form +F / -F (Algorithm 1)
+    perm = np.random.default_rng(3).permutation(g.nnz)
+    other = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 3, 3, sched, seed=2, order=perm)
+    assert np.abs(other.sum(0) - Y0.astype(np.float64).sum(0)).max() < 1e-12
+    assert not np.array_equal(other, csr)
+    with pytest.raises(ValueError):
+        oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 1, 3, sched, order=np.zeros(g.nnz, dtype=np.int64))
+
+
 def test_actual_energy_tracks_effective_energy():
     # Fig. 3(a): the energy accumulated from the drawn pairs converges to the
     # degree-weighted objective evaluated after each epoch.
