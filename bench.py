@@ -238,7 +238,10 @@ def run_snap(args, rank, world, local_rank):
     nnz = int(row_ptr[-1])
     k = args.k
     mode = {"hogwild": snap.MODE_HOGWILD, "hogwild_red": snap.MODE_HOGWILD_RED, "sync": snap.MODE_SYNC}[args.mode]
-    opts = snap.make_options(mode=mode, sync_substeps=16 if mode == snap.MODE_SYNC else 1)
+    # the synchronous mode needs its step cap on hub-heavy graphs: a hub's
+    # frozen-position step sums ~10^5 pulls
+    opts = snap.make_options(mode=mode, sync_substeps=16 if mode == snap.MODE_SYNC else 1,
+                             sync_cap=1.0 if mode == snap.MODE_SYNC else 0.0)
     sched = snap.linear_schedule(eta0=1.0, total_epochs=EPOCHS)
     seed = args.seed + rank
     Y0 = initial_positions(n, args.seed)
@@ -293,7 +296,37 @@ def run_snap(args, rank, world, local_rank):
         o0 = snap.snap_layout_objective(h, Y0_d, k, False, 20_000_000, 5, stream)[2]
         o1 = snap.snap_layout_objective(h, Y, k, False, 20_000_000, 5, stream)[2]
         extras["objective_sampled"] = {"initial": o0, "final": o1}
+        extras["device_bytes"] = snap.snap_layout_device_bytes(h)
     snap.snap_layout_destroy(h)
+    if rank == 0 and not args.no_extras:
+        # the other modes on the same graph, 5 epochs each (not the headline)
+        for mname, mcode in (("hogwild_red", snap.MODE_HOGWILD_RED), ("sync", snap.MODE_SYNC)):
+            if mcode == mode:
+                continue
+            o2 = snap.make_options(mode=mcode, sync_substeps=16, sync_cap=1.0)
+            h2 = snap.snap_layout_create(row_ptr, col_idx, None, n, o2, stream)
+            Y.copy_(Y0_d)
+            snap.snap_layout_epochs(h2, Y, 0, 1, k, sched, seed, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            snap.snap_layout_epochs(h2, Y, 1, 5, k, sched, seed, stream)
+            e1.record(stream)
+            snap.snap_layout_check(h2, stream)
+            ms = e0.elapsed_time(e1) / 5
+            extras[f"mode_{mname}"] = {"ms_per_epoch": ms, "updates_per_s": nnz * (1 + k) / (ms / 1e3),
+                                       "options": "S=16, cap=1.0" if mcode == snap.MODE_SYNC else "default"}
+            snap.snap_layout_destroy(h2)
+
+    # ceiling of the access pattern that binds the epoch kernel: random
+    # dependent read-modify-writes of 8-byte slots in an L2-resident array
+    # of the same size as the positions, measured now by the probe kernel
+    rmw_peak = None
+    if not args.no_extras:
+        from paper_2608_01907_gb300 import probe
+        scratch = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+        op = "load_dep_atomic" if mode == snap.MODE_HOGWILD_RED else "load_store"
+        rmw_peak = max(probe.random_access_rate(scratch, op, depth=d, iters=32) for d in (1, 4))
+        del scratch
 
     # roofline of the epoch kernel: algorithmic bytes per launch
     deg = np.diff(row_ptr)
@@ -308,6 +341,17 @@ def run_snap(args, rank, world, local_rank):
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": float(np.mean(launch_ms)),
             "peak_source": f"{peak_kind} hbm_gbs (copy)"}
     del avg_launch_s
+    roof_l2 = None
+    if rmw_peak and mode != snap.MODE_SYNC:
+        # per undirected edge the oriented kernel read-modify-writes the
+        # partner once and 2k negatives once each
+        rmw_per_launch = (nnz // 2) * (1 + 2 * k)
+        ach = rmw_per_launch / (float(np.mean(launch_ms)) / 1e3)
+        roof_l2 = {"bound": "l2 dependent read-modify-write (random 8-byte slots)", "achieved": ach / 1e9,
+                   "peak": rmw_peak / 1e9, "unit": "G RMW/s", "frac": ach / rmw_peak,
+                   "rmw_per_launch": rmw_per_launch,
+                   "peak_source": "probe kernel (csrc/probe_l2.cu) measured in this run on an L2-resident array "
+                                  "of n float2 slots"}
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -346,7 +390,7 @@ def run_snap(args, rank, world, local_rank):
                            "l2": "inputs larger than L2: the 272 MB edge stream is re-read every epoch; the "
                                  "33.5 MB positions stay L2-resident by design",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "roofline_l2": roof_l2, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * EPOCHS * launches_per_epoch, "clocks": clk}
         line.update(extras)
         print(json.dumps(line), flush=True)

@@ -53,15 +53,20 @@ typedef enum {
 
 /* Parallel update semantics of an epoch. */
 typedef enum {
-    /* Lock-free updates in the spirit of HOGWILD! (Section 3.4): every lane
-     * owns a run of consecutive directed edges (a slice of a source bundle,
-     * Section 3.4), keeps y_i in registers while it walks them and writes the
-     * partners y_j, y_s back with plain racy stores.  Concurrent writers may
-     * overwrite each other. */
+    /* Lock-free updates in the spirit of HOGWILD! (Section 3.4).  Each
+     * undirected edge {i, j} is placed in the bundle of its higher-ranked
+     * endpoint (larger degree, then smaller id); a lane takes whole bundles
+     * (long ones are cut into pieces), in an order reshuffled every epoch,
+     * keeps the bundle's source in registers, and applies both directed
+     * steps (i, j) and (j, i) of every entry, each with its own negatives.
+     * Partners are written back with plain racy stores: concurrent writers
+     * may overwrite each other. */
     SNAP_MODE_HOGWILD = 0,
     /* As HOGWILD, but partner updates are atomic float adds (no lost
-     * updates); a source bundle split over L lanes merges its L displacements
-     * by averaging. */
+     * updates); a bundle cut into L pieces merges the L source displacements
+     * by averaging.  Faster, but more sensitive to concurrency on small or
+     * dense graphs (concurrent additive pulls on one vertex act like a
+     * larger step). */
     SNAP_MODE_HOGWILD_RED = 1,
     /* Deterministic synchronous mode: positions are frozen within each of S
      * row chunks, every force is quantised to int64 fixed point (2^-32) and
@@ -97,7 +102,10 @@ typedef struct {
     const float *node_weights;/* host, n; SNAP_SAMPLER_WEIGHTS only (unused now) */
     int32_t sync_substeps;    /* S >= 1 row chunks per epoch in SNAP_MODE_SYNC */
     float sync_cap;           /* > 0: clip each node's sync step to cap*eta_t/eta0 */
-    int32_t segment_edges;    /* directed edges per lane segment; 0 = default (32); multiple of 4 */
+    int32_t segment_edges;    /* work per lane segment, a multiple of 4 in [4, 4096]: oriented entries
+                                 (2 directed edges each) in the HOGWILD modes, directed edges in SYNC;
+                                 0 = default (HOGWILD: 32 for large graphs, 128 for small ones;
+                                 SYNC: 32) */
     int32_t block_threads;    /* threads per block; 0 = default (256) */
 } snap_options;
 

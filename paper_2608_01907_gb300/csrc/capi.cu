@@ -62,6 +62,15 @@ cudaError_t dev_alloc(AllocCounter &ac, void **p, size_t bytes) {
     return cudaMalloc(p, bytes < 16 ? 16 : bytes);
 }
 
+// SplitMix64 finaliser (Steele, Lea, Flood 2014): the per-epoch offset of
+// the segment order.
+uint64_t mix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
 double step_size(const snap_schedule &s, int32_t t) {
     if (s.kind == 1) return s.eta0;
     const double T = s.total_epochs > 0 ? (double)s.total_epochs : 1.0;
@@ -89,28 +98,49 @@ struct snap_layout {
     int32_t *d_seg_row = nullptr;
     int32_t *d_deg = nullptr;
     long long *d_disp = nullptr;
+    // oriented bundle list (HOGWILD modes): one entry per undirected edge,
+    // whole rows packed into segments of about act_seg_len entries
+    int64_t act_nnz = 0;
+    int64_t act_num_segs = 0;
+    int32_t act_seg_len = 32;
+    int64_t perm_mul = 1;
+    int64_t *d_act_row_ptr = nullptr;
+    int4 *d_act_ent = nullptr;
+    int4 *d_act_seg = nullptr;
     uint32_t *d_status = nullptr;   // [0] fault bits, [1] validation bits
     double *d_partial = nullptr;    // 2 * kObjGrid
     uint32_t *h_status = nullptr;   // pinned mirror of d_status[0]
     cudaEvent_t status_event = nullptr;
     bool status_pending = false;
-    int grid_hog = 0, grid_red = 0, grid_sync = 0, grid_apply = 0;
+    int sms = 1;
+    int grid_sync = 0, grid_apply = 0;
+    int grid_oriented[2][5] = {{0}};   // [red][min(k, 4)], filled on first use
     std::vector<int64_t> chunk_edges;   // S + 1 edge offsets of the sync chunks
     int64_t device_bytes = 0;
 
-    void release() {
+    void release_csr() {
         cudaFree(d_row_ptr);
         cudaFree(d_col);
         cudaFree(d_seg_row);
+        d_row_ptr = nullptr;
+        d_col = nullptr;
+        d_seg_row = nullptr;
+    }
+
+    void release() {
+        release_csr();
+        cudaFree(d_act_row_ptr);
+        cudaFree(d_act_ent);
+        cudaFree(d_act_seg);
+        d_act_row_ptr = nullptr;
+        d_act_ent = nullptr;
+        d_act_seg = nullptr;
         cudaFree(d_deg);
         cudaFree(d_disp);
         cudaFree(d_status);
         cudaFree(d_partial);
         if (h_status) cudaFreeHost(h_status);
         if (status_event) cudaEventDestroy(status_event);
-        d_row_ptr = nullptr;
-        d_col = nullptr;
-        d_seg_row = nullptr;
         d_deg = nullptr;
         d_disp = nullptr;
         d_status = nullptr;
@@ -119,6 +149,134 @@ struct snap_layout {
         status_event = nullptr;
     }
 };
+
+static int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Segments of the oriented list: whole rows packed greedily up to `target`
+// entries; a row longer than `target` is cut into equal pieces.
+static void pack_segments(const std::vector<int64_t> &rp, int32_t target, std::vector<int4> &out) {
+    out.clear();
+    const int32_t n = (int32_t)rp.size() - 1;
+    int64_t open_begin = -1, open_end = 0;
+    int32_t open_row = 0;
+    auto close = [&]() {
+        if (open_begin >= 0) out.push_back(make_int4((int)open_begin, (int)open_end, open_row, 1));
+        open_begin = -1;
+    };
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t len = rp[(size_t)i + 1] - rp[(size_t)i];
+        if (len == 0) continue;
+        if (len > target) {
+            close();
+            const int64_t pieces = (len + target - 1) / target;
+            for (int64_t q = 0; q < pieces; ++q) {
+                const int64_t b = rp[(size_t)i] + len * q / pieces;
+                const int64_t e = rp[(size_t)i] + len * (q + 1) / pieces;
+                out.push_back(make_int4((int)b, (int)e, i, (int)pieces));
+            }
+            continue;
+        }
+        if (open_begin >= 0 && open_end - open_begin + len > target) close();
+        if (open_begin < 0) {
+            open_begin = rp[(size_t)i];
+            open_row = i;
+        }
+        open_end = rp[(size_t)i + 1];
+    }
+    close();
+}
+
+// Builds the oriented bundle list from the validated device CSR and then
+// frees the CSR (the HOGWILD kernels and the objective need only the list).
+static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t stream) {
+    const int32_t n = h->n;
+    const int64_t nnz = h->nnz;
+    h->act_nnz = nnz / 2;   // symmetric and loop-free: each undirected edge once
+    if (h->act_seg_len == 0) {
+        // Default segment size.  Concurrency degrades Hogwild quality when a
+        // large share of the graph is in flight at once, so graphs that fill
+        // the device's lanes (about 512 per SM) fewer than four times over at
+        // 32 entries per segment get 128-entry segments; larger graphs get 32
+        // (shorter tails, same quality: their in-flight share is small).
+        const int64_t lanes = (int64_t)h->sms * 512;
+        h->act_seg_len = h->act_nnz >= 4 * 32 * lanes ? 32 : 128;
+    }
+    int32_t *flags = nullptr, *pos = nullptr;
+    void *temp = nullptr;
+    size_t temp_bytes = 0;
+    cudaError_t err = cudaSuccess;
+    const char *what = "";
+    auto alloc = [&](void **p, size_t bytes, bool keep, const char *nm) {
+        if (err != cudaSuccess) return;
+        err = dev_alloc(ac, p, bytes);
+        if (err != cudaSuccess) {
+            what = nm;
+        } else if (keep) {
+            h->device_bytes += (int64_t)bytes;
+        }
+    };
+    auto step = [&](cudaError_t e, const char *nm) {
+        if (err == cudaSuccess && e != cudaSuccess) {
+            err = e;
+            what = nm;
+        }
+    };
+    alloc((void **)&h->d_act_row_ptr, sizeof(int64_t) * ((size_t)n + 1), true, "oriented row offsets");
+    alloc((void **)&h->d_act_ent, sizeof(int4) * (size_t)(h->act_nnz > 0 ? h->act_nnz : 1), true, "oriented entries");
+    alloc((void **)&flags, sizeof(int32_t) * ((size_t)nnz + 1), false, "orientation flags");
+    alloc((void **)&pos, sizeof(int32_t) * ((size_t)nnz + 1), false, "orientation offsets");
+    if (err == cudaSuccess) step(exclusive_scan_i32(nullptr, &temp_bytes, flags, pos, nnz + 1, stream), "scan size");
+    alloc(&temp, temp_bytes, false, "scan scratch");
+    if (err == cudaSuccess) {
+        step(launch_orient_flags(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, flags, stream),
+             "orientation flags kernel");
+        step(exclusive_scan_i32(temp, &temp_bytes, flags, pos, nnz + 1, stream), "orientation scan");
+        step(launch_orient_scatter(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, pos,
+                                   h->d_act_ent, stream), "orientation scatter kernel");
+        step(launch_orient_rowptr(h->d_row_ptr, pos, n, h->d_act_row_ptr, stream), "orientation offsets kernel");
+    }
+    std::vector<int64_t> act_rp;
+    if (err == cudaSuccess) {
+        act_rp.resize((size_t)n + 1);
+        step(cudaMemcpyAsync(act_rp.data(), h->d_act_row_ptr, sizeof(int64_t) * ((size_t)n + 1),
+                             cudaMemcpyDeviceToHost, stream), "read oriented row offsets");
+        step(cudaStreamSynchronize(stream), "orientation");
+    }
+    cudaFree(flags);
+    cudaFree(pos);
+    cudaFree(temp);
+    if (err != cudaSuccess) return cuda_fail(err, what);
+    if (act_rp[(size_t)n] != h->act_nnz)
+        return fail(SNAP_ERR_CUDA, "orientation produced %lld entries, expected %lld", (long long)act_rp[(size_t)n],
+                    (long long)h->act_nnz);
+    std::vector<int4> segs;
+    pack_segments(act_rp, h->act_seg_len, segs);
+    h->act_num_segs = (int64_t)segs.size();
+    alloc((void **)&h->d_act_seg, sizeof(int4) * (segs.empty() ? 1 : segs.size()), true, "oriented segments");
+    if (err == cudaSuccess && !segs.empty()) {
+        step(cudaMemcpyAsync(h->d_act_seg, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, stream),
+             "copy oriented segments");
+        step(cudaStreamSynchronize(stream), "copy oriented segments");
+    }
+    if (err != cudaSuccess) return cuda_fail(err, what);
+    // segment order multiplier: coprime with the segment count, near its golden section
+    int64_t m = (int64_t)(0.6180339887498949 * (double)h->act_num_segs) | 1;
+    while (h->act_num_segs > 1 && gcd64(m, h->act_num_segs) != 1) m += 2;
+    h->perm_mul = h->act_num_segs > 1 ? m % h->act_num_segs : 0;
+    if (h->act_num_segs > 1 && h->perm_mul == 0) h->perm_mul = 1;
+    h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
+                                 sizeof(int32_t) * (size_t)(h->num_segs * h->seg_len + 4) +
+                                 sizeof(int32_t) * (size_t)(h->num_segs > 0 ? h->num_segs : 1));
+    h->release_csr();
+    return SNAP_OK;
+}
 
 extern "C" {
 
@@ -190,7 +348,10 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     h->n = n;
     h->nnz = row_ptr[n];
     h->opts = o;
-    h->seg_len = o.segment_edges ? o.segment_edges : 32;
+    // CSR segments: the synchronous kernel's unit of work (and the
+    // validation pass); the HOGWILD modes use segments of oriented entries.
+    h->seg_len = (o.mode == SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 32;
+    h->act_seg_len = (o.mode != SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 0;   // 0: by size
     h->block = o.block_threads ? o.block_threads : 256;
     h->num_segs = (h->nnz + h->seg_len - 1) / h->seg_len;
 
@@ -268,11 +429,21 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
-    h->grid_hog = sms * hogwild_blocks_per_sm(0, h->block);
-    h->grid_red = sms * hogwild_blocks_per_sm(1, h->block);
+    h->sms = sms;
     h->grid_sync = sms * sync_blocks_per_sm(h->block);
     h->grid_apply = sms * 8;
     cudaGetLastError();
+
+    if (o.mode != SNAP_MODE_SYNC && h->nnz > 0) {
+        st = build_oriented(h, ac, stream);
+        if (st != SNAP_OK) {
+            cudaStreamSynchronize(stream);
+            h->release();
+            delete h;
+            cudaGetLastError();
+            return st;
+        }
+    }
 
     const int32_t S = o.sync_substeps;
     h->chunk_edges.assign((size_t)S + 1, 0);
@@ -365,24 +536,29 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
                                             h->grid_apply, 256, stream);
             }
         } else {
-            EpochArgs a;
-            a.row_ptr = h->d_row_ptr;
-            a.col_idx = h->d_col;
-            a.seg_row = h->d_seg_row;
+            OrientedArgs a;
+            a.row_ptr = h->d_act_row_ptr;
+            a.ent = h->d_act_ent;
+            a.seg = h->d_act_seg;
             a.pos = pos;
-            a.nnz = h->nnz;
+            a.num_segs = h->act_num_segs;
+            a.perm_mul = h->perm_mul;
+            a.perm_add = (int64_t)(mix64(seed ^ (0x5EC0ull * (uint64_t)(t + 1))) % (uint64_t)h->act_num_segs);
             a.n = h->n;
             a.k = neg_samples;
-            a.seg_len = h->seg_len;
             a.epoch = (uint32_t)t;
             a.seed = seed;
             a.eta = (float)eta;
             a.status = h->d_status;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
-            const int gmax = red ? h->grid_red : h->grid_hog;
-            const int64_t want = (h->num_segs + h->block - 1) / h->block;
+            const int g = neg_samples < 4 ? neg_samples : 4;
+            if (h->grid_oriented[red][g] == 0)
+                h->grid_oriented[red][g] = h->sms * oriented_blocks_per_sm(red, neg_samples, h->block);
+            const int gmax = h->grid_oriented[red][g];
+            const int64_t want = (h->act_num_segs + h->block - 1) / h->block;
+            if (h->act_num_segs == 0) continue;
             const int grid = (int)(want < gmax ? want : gmax);
-            err = launch_hogwild_epoch(a, red, grid, h->block, stream);
+            err = launch_oriented_epoch(a, red, grid > 0 ? grid : 1, h->block, stream);
         }
         if (err != cudaSuccess) return cuda_fail(err, "epoch launch");
     }
@@ -426,9 +602,14 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     const float2 *pos = reinterpret_cast<const float2 *>(positions);
     cudaError_t err = cudaMemsetAsync(h->d_partial, 0, sizeof(double) * 2 * kObjGrid, stream);
-    if (err == cudaSuccess && h->nnz > 0)
-        err = launch_objective_edges(h->d_row_ptr, h->d_col, h->d_seg_row, pos, h->nnz, h->n, h->seg_len,
-                                     h->d_partial, kObjGrid, stream);
+    if (err == cudaSuccess && h->nnz > 0) {
+        if (h->d_col)
+            err = launch_objective_edges(h->d_row_ptr, h->d_col, h->d_seg_row, pos, h->nnz, h->seg_len,
+                                         h->d_partial, kObjGrid, stream);
+        else if (h->act_num_segs > 0)
+            err = launch_objective_oriented(h->d_act_row_ptr, h->d_act_ent, h->d_act_seg, h->act_num_segs, pos,
+                                            h->d_partial, kObjGrid, stream);
+    }
     if (err == cudaSuccess && h->n > 1) {
         if (exact)
             err = launch_objective_pairs_exact(pos, h->d_deg, h->n, h->d_partial + kObjGrid, kObjGrid, stream);

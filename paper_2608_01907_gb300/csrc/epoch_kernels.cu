@@ -1,24 +1,19 @@
 // epoch_kernels.cu -- one epoch of edge-centric negative sampling
 // (Algorithm 1, Section 3.3) on sm_103a.
 //
-// Work decomposition.  The directed edges are the CSR entries, row-major, so
-// the out-edges of a source i -- its "bundle" (Section 3.4) -- are contiguous.
-// The edge array is cut into fixed segments of seg_len edges; lane w of the
-// grid owns segment w and walks it in order, keeping the current source's
-// position in registers and switching source at row boundaries (the start
-// row of every segment is precomputed in seg_row).  Every lane thus runs
-// Algorithm 1 sequentially over a contiguous slice of source bundles, like
-// one thread of the paper's bundle scheme; a bundle longer than a segment is
-// split over several lanes.  Consecutive lanes own consecutive segments, so a
-// warp streams a contiguous run of col_idx.
+// HOGWILD modes work on oriented bundles (built by capi.cu at create):
+// every undirected edge {i, j} is listed once, in the row of its
+// higher-ranked endpoint (degree, then smaller id), with the CSR indices of
+// both directed copies.  Rows are packed whole into segments of about 32
+// entries (rows longer than that are cut into pieces); lane w of the grid
+// takes segment perm_t(w), an affine permutation of the segment ids that
+// changes every epoch (the shuffle before bundling of Section 3.4), keeps
+// the source y_i in registers while it walks its rows, and applies both
+// directed steps of every entry.
 //
-// Per directed edge e = (i, j):
-//   y_j, and the k negatives s_m = negative(word m of Philox(e, t)), are
-//   gathered (L2-resident positions); the attraction F^a(y_i - y_j) is
-//   applied as y_i += eta F, y_j -= eta F; then for each m the repulsion
-//   F^r(y_i - y_s) as y_i += eta G, y_s -= eta G, each from the current y_i.
-//   A partner drawn twice in one step (s == j, or s_m == s_m') sees its
-//   earlier update through registers, as in the sequential algorithm.
+// The synchronous mode walks the full CSR (all directed edges, row-major)
+// in fixed segments with positions frozen, accumulating int64 fixed-point
+// displacements.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,122 +34,182 @@ __device__ __forceinline__ void apply_partner(float2 *pos, int32_t idx, float2 n
     }
 }
 
+// ---------------------------------------------------------------------------
+// Oriented bundles.  Every undirected edge {i, j} is listed once, in the row
+// of its higher-ranked endpoint i (degree, then smaller id), with the CSR
+// indices of both directed copies.  The lane owning that row applies both
+// directed steps of Algorithm 1 back to back: (i, j) with the negatives of
+// source i (keyed by the index of (i, j)), then (j, i) with the negatives of
+// source j (keyed by the index of (j, i)).  Each directed edge is processed
+// once per epoch with its own random words, as in Algorithm 1; only the order
+// differs.  A vertex is then a partner only of its higher-ranked neighbours
+// (at most a few hundred even when the top degree is ~10^5), which removes
+// the same-address read-after-write chains that hubs cause when they are the
+// partner of every neighbour's bundle.
+// ---------------------------------------------------------------------------
+
+// Negatives of one group (up to 4, already gathered into v[]) for source
+// `src` held in ysrc; the vertex `other` is register-resident in yoth.
+// s[] and v[] are updated in place (v[m] = the value after its update).
 template <bool RED>
-__device__ __forceinline__ void write_source(const EpochArgs &a, int32_t row, float2 yi, float2 yi0,
-                                             uint32_t &flags) {
+__device__ __forceinline__ void negative_group(float2 *pos, float eta, const int32_t (&s)[4], float2 (&v)[4], int nm,
+                                               float2 &ysrc, int32_t other, float2 &yoth) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (m < nm) {
+            float2 x = v[m];
+#pragma unroll
+            for (int p = 0; p < m; ++p)
+                if (s[p] == s[m]) x = v[p];
+            if (s[m] == other) x = yoth;
+            const float2 gr = repulsion_on_i(ysrc.x - x.x, ysrc.y - x.y);
+            const float2 dg = make_float2(eta * gr.x, eta * gr.y);
+            ysrc.x += dg.x;
+            ysrc.y += dg.y;
+            x.x -= dg.x;
+            x.y -= dg.y;
+            if (s[m] == other)
+                yoth = x;
+            else
+                apply_partner<RED>(pos, s[m], x, make_float2(-dg.x, -dg.y));
+            v[m] = x;
+        }
+    }
+}
+
+// Groups 1, 2, ... of negatives (k > 4): gathered after the earlier stores
+// of this lane, so memory already holds this lane's updates.
+template <bool RED>
+__device__ __forceinline__ void later_negatives(const OrientedArgs &a, int64_t ekey, int32_t src, float2 &ysrc,
+                                                int32_t other, float2 &yoth, uint2 key, uint32_t nm1) {
+    for (int g = 1; g * 4 < a.k; ++g) {
+        const int nm = a.k - 4 * g < 4 ? a.k - 4 * g : 4;
+        const uint4 w = edge_words(ekey, a.epoch, (uint32_t)g, key);
+        int32_t s[4] = {negative_of(w.x, src, nm1), negative_of(w.y, src, nm1), negative_of(w.z, src, nm1),
+                        negative_of(w.w, src, nm1)};
+        float2 v[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (m < nm) v[m] = load_pos(a.pos + s[m]);
+        negative_group<RED>(a.pos, a.eta, s, v, nm, ysrc, other, yoth);
+    }
+}
+
+template <bool RED, int G>
+__device__ __forceinline__ void oriented_entry(const OrientedArgs &a, int32_t i, int32_t j, int32_t e1, int32_t e2,
+                                               float2 &yi, uint2 key, uint32_t nm1) {
+    const float eta = a.eta;
+    int32_t s1[4] = {0, 0, 0, 0}, s2[4] = {0, 0, 0, 0};
+    float2 v1[4], v2[4];
+    if (G > 0) {
+        const uint4 w1 = edge_words(e1, a.epoch, 0u, key);
+        const uint4 w2 = edge_words(e2, a.epoch, 0u, key);
+        s1[0] = negative_of(w1.x, i, nm1);
+        s1[1] = negative_of(w1.y, i, nm1);
+        s1[2] = negative_of(w1.z, i, nm1);
+        s1[3] = negative_of(w1.w, i, nm1);
+        s2[0] = negative_of(w2.x, j, nm1);
+        s2[1] = negative_of(w2.y, j, nm1);
+        s2[2] = negative_of(w2.z, j, nm1);
+        s2[3] = negative_of(w2.w, j, nm1);
+    }
+    const bool prefetch2 = a.k <= 4;   // group 0 of direction 2 can be gathered up front
+    float2 yj = load_pos(a.pos + j);
+#pragma unroll
+    for (int m = 0; m < G; ++m) v1[m] = load_pos(a.pos + s1[m]);
+    if (prefetch2) {
+#pragma unroll
+        for (int m = 0; m < G; ++m) v2[m] = load_pos(a.pos + s2[m]);
+    }
+    const float2 yj0 = yj;
+
+    // direction 1: (i, j), source i
+    {
+        const float2 f = attraction_on_i(yi.x - yj.x, yi.y - yj.y);
+        const float2 df = make_float2(eta * f.x, eta * f.y);
+        yi.x += df.x;
+        yi.y += df.y;
+        yj.x -= df.x;
+        yj.y -= df.y;
+        if (G > 0) negative_group<RED>(a.pos, eta, s1, v1, G, yi, j, yj);
+        if (a.k > 4) later_negatives<RED>(a, e1, i, yi, j, yj, key, nm1);
+    }
+    // direction 2: (j, i), source j
+    {
+        const float2 f = attraction_on_i(yj.x - yi.x, yj.y - yi.y);
+        const float2 df = make_float2(eta * f.x, eta * f.y);
+        yj.x += df.x;
+        yj.y += df.y;
+        yi.x -= df.x;
+        yi.y -= df.y;
+        if (G > 0) {
+            if (prefetch2) {
+                // a negative of j that direction 1 already moved is taken from registers
+#pragma unroll
+                for (int m = 0; m < G; ++m)
+#pragma unroll
+                    for (int q = 0; q < G; ++q)
+                        if (s1[q] == s2[m]) v2[m] = v1[q];
+            } else {
+#pragma unroll
+                for (int m = 0; m < G; ++m) v2[m] = load_pos(a.pos + s2[m]);
+            }
+            negative_group<RED>(a.pos, eta, s2, v2, G, yj, i, yi);
+        }
+        if (a.k > 4) later_negatives<RED>(a, e2, j, yj, i, yi, key, nm1);
+    }
+    apply_partner<RED>(a.pos, j, yj, make_float2(yj.x - yj0.x, yj.y - yj0.y));
+}
+
+// Source write-back at the end of a row run.  HOGWILD stores the lane's copy;
+// HOGWILD_RED adds the lane's displacement, divided by the number of pieces
+// a long row was cut into, so a split bundle takes one sequential pass's step.
+template <bool RED>
+__device__ __forceinline__ void write_oriented_source(const OrientedArgs &a, int32_t row, float2 yi, float2 yi0,
+                                                      int pieces, uint32_t &flags) {
     if (!finite2(yi)) flags |= kStatusNonFinite;
     if (RED) {
-        // A bundle split over L segments merges its L source displacements
-        // by their mean, so the source takes one sequential pass's step.
-        const int64_t rb = __ldg(a.row_ptr + row);
-        const int64_t re = __ldg(a.row_ptr + row + 1);
-        const int64_t L = (re - 1) / a.seg_len - rb / a.seg_len + 1;
-        const float inv = L > 1 ? 1.0f / (float)L : 1.0f;
+        const float inv = pieces > 1 ? 1.0f / (float)pieces : 1.0f;
         atomicAdd(a.pos + row, make_float2((yi.x - yi0.x) * inv, (yi.y - yi0.y) * inv));
     } else {
         store_pos(a.pos + row, yi);
     }
 }
 
-template <bool RED>
-__device__ __forceinline__ void hogwild_edge(const EpochArgs &a, int64_t e, int32_t i, int32_t j,
-                                             float2 &yi, uint2 key, uint32_t nm1) {
-    const float eta = a.eta;
-    // first group of up to four negatives is gathered together with y_j
-    int32_t s[4];
-    float2 ys[4];
-    int nm = a.k < 4 ? a.k : 4;
-    {
-        const uint4 w = edge_words(e, a.epoch, 0u, key);
-        s[0] = negative_of(w.x, i, nm1);
-        s[1] = negative_of(w.y, i, nm1);
-        s[2] = negative_of(w.z, i, nm1);
-        s[3] = negative_of(w.w, i, nm1);
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-        if (m < nm) ys[m] = load_pos(a.pos + s[m]);
-    float2 yj = load_pos(a.pos + j);
+#ifndef SNAP_ORIENTED_MIN_BLOCKS
+#define SNAP_ORIENTED_MIN_BLOCKS 1
+#endif
 
-    // attraction (Table 1), evaluated once from the positions before the step
-    const float2 f = attraction_on_i(yi.x - yj.x, yi.y - yj.y);
-    const float2 df = make_float2(eta * f.x, eta * f.y);
-    yi.x += df.x;
-    yi.y += df.y;
-    yj.x -= df.x;
-    yj.y -= df.y;
-    apply_partner<RED>(a.pos, j, yj, make_float2(-df.x, -df.y));
-
-    // repulsion from each negative (Table 1), immediate updates
-    for (int g = 0; g * 4 < a.k; ++g) {
-        if (g > 0) {
-            nm = a.k - 4 * g < 4 ? a.k - 4 * g : 4;
-            const uint4 w = edge_words(e, a.epoch, (uint32_t)g, key);
-            s[0] = negative_of(w.x, i, nm1);
-            s[1] = negative_of(w.y, i, nm1);
-            s[2] = negative_of(w.z, i, nm1);
-            s[3] = negative_of(w.w, i, nm1);
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (m < nm) ys[m] = load_pos(a.pos + s[m]);
-        }
-        float2 upd[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            if (m < nm) {
-                float2 v = ys[m];
-                if (g == 0 && s[m] == j) v = yj;
-#pragma unroll
-                for (int p = 0; p < m; ++p)
-                    if (s[p] == s[m]) v = upd[p];
-                const float2 gr = repulsion_on_i(yi.x - v.x, yi.y - v.y);
-                const float2 dg = make_float2(eta * gr.x, eta * gr.y);
-                yi.x += dg.x;
-                yi.y += dg.y;
-                v.x -= dg.x;
-                v.y -= dg.y;
-                upd[m] = v;
-                apply_partner<RED>(a.pos, s[m], v, make_float2(-dg.x, -dg.y));
-            }
-        }
-    }
-}
-
-template <bool RED>
-__global__ void __launch_bounds__(256) hogwild_epoch_kernel(const EpochArgs a) {
-    const int64_t num_segs = (a.nnz + a.seg_len - 1) / a.seg_len;
+template <bool RED, int G>
+__global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_kernel(const OrientedArgs a) {
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
     const uint32_t nm1 = (uint32_t)(a.n - 1);
     uint32_t flags = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; seg < num_segs; seg += stride) {
-        const int64_t e0 = seg * a.seg_len;
-        const int64_t e1 = min(e0 + (int64_t)a.seg_len, a.nnz);
-        int32_t row = __ldg(a.seg_row + seg);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.num_segs; w += stride) {
+        const int64_t ws = (int64_t)(((uint64_t)a.perm_mul * (uint64_t)w + (uint64_t)a.perm_add) %
+                                     (uint64_t)a.num_segs);
+        const int4 sg = __ldg(a.seg + ws);   // {begin, end, first row, pieces}
+        int64_t p = sg.x;
+        const int64_t p1 = sg.y;
+        int32_t row = sg.z;
         int64_t row_end = __ldg(a.row_ptr + row + 1);
         float2 yi = load_pos(a.pos + row);
         float2 yi0 = yi;
-        for (int64_t eb = e0; eb < e1; eb += 4) {
-            const int4 c4 = load_cols4(a.col_idx + eb);
-            const int32_t cols[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t e = eb + q;
-                if (e < e1) {
-                    if (e >= row_end) {
-                        write_source<RED>(a, row, yi, yi0, flags);
-                        do {
-                            ++row;
-                            row_end = __ldg(a.row_ptr + row + 1);
-                        } while (row_end <= e);
-                        yi = load_pos(a.pos + row);
-                        yi0 = yi;
-                    }
-                    hogwild_edge<RED>(a, e, row, cols[q], yi, key, nm1);
-                }
+        for (; p < p1; ++p) {
+            if (p >= row_end) {
+                write_oriented_source<RED>(a, row, yi, yi0, 1, flags);
+                do {
+                    ++row;
+                    row_end = __ldg(a.row_ptr + row + 1);
+                } while (row_end <= p);
+                yi = load_pos(a.pos + row);
+                yi0 = yi;
             }
+            const int4 en = load_entry(a.ent + p);   // {j, index of (i, j), index of (j, i), -}
+            oriented_entry<RED, G>(a, row, en.x, en.y, en.z, yi, key, nm1);
         }
-        write_source<RED>(a, row, yi, yi0, flags);
+        write_oriented_source<RED>(a, row, yi, yi0, sg.w, flags);
     }
     if (flags) atomicOr(a.status, flags);
 }
@@ -274,14 +329,6 @@ __global__ void __launch_bounds__(256) sync_apply_kernel(float2 *pos, long long 
 
 }  // namespace
 
-cudaError_t launch_hogwild_epoch(const EpochArgs &a, int red_mode, int grid, int block, cudaStream_t s) {
-    if (red_mode)
-        hogwild_epoch_kernel<true><<<grid, block, 0, s>>>(a);
-    else
-        hogwild_epoch_kernel<false><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_sync_chunk(const SyncArgs &a, int grid, int block, cudaStream_t s) {
     sync_chunk_kernel<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
@@ -293,13 +340,47 @@ cudaError_t launch_sync_apply(float2 *pos, long long *disp, int32_t n, float eta
     return cudaGetLastError();
 }
 
-int hogwild_blocks_per_sm(int red_mode, int block) {
+template <bool RED>
+static cudaError_t launch_oriented_g(const OrientedArgs &a, int grid, int block, cudaStream_t s) {
+    switch (a.k < 4 ? a.k : 4) {
+        case 0: oriented_epoch_kernel<RED, 0><<<grid, block, 0, s>>>(a); break;
+        case 1: oriented_epoch_kernel<RED, 1><<<grid, block, 0, s>>>(a); break;
+        case 2: oriented_epoch_kernel<RED, 2><<<grid, block, 0, s>>>(a); break;
+        case 3: oriented_epoch_kernel<RED, 3><<<grid, block, 0, s>>>(a); break;
+        default: oriented_epoch_kernel<RED, 4><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s) {
+    return red_mode ? launch_oriented_g<true>(a, grid, block, s) : launch_oriented_g<false>(a, grid, block, s);
+}
+
+template <bool RED, int G>
+static int oriented_occupancy(int block) {
     int nb = 0;
-    if (red_mode)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hogwild_epoch_kernel<true>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hogwild_epoch_kernel<false>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, oriented_epoch_kernel<RED, G>, block, 0);
     return nb > 0 ? nb : 1;
+}
+
+int oriented_blocks_per_sm(int red_mode, int k, int block) {
+    const int g = k < 4 ? k : 4;
+    if (red_mode) {
+        switch (g) {
+            case 0: return oriented_occupancy<true, 0>(block);
+            case 1: return oriented_occupancy<true, 1>(block);
+            case 2: return oriented_occupancy<true, 2>(block);
+            case 3: return oriented_occupancy<true, 3>(block);
+            default: return oriented_occupancy<true, 4>(block);
+        }
+    }
+    switch (g) {
+        case 0: return oriented_occupancy<false, 0>(block);
+        case 1: return oriented_occupancy<false, 1>(block);
+        case 2: return oriented_occupancy<false, 2>(block);
+        case 3: return oriented_occupancy<false, 3>(block);
+        default: return oriented_occupancy<false, 4>(block);
+    }
 }
 
 int sync_blocks_per_sm(int block) {

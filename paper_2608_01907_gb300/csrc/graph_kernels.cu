@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cub/device/device_scan.cuh>
+
 #include "snap_device.cuh"
 #include "snap_internal.h"
 
@@ -75,6 +77,72 @@ __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const i
     if (flags) atomicOr(flags_out, flags);
 }
 
+// Orientation of the undirected edges: {i, j} belongs to the bundle of the
+// endpoint that ranks higher by (degree, then smaller id).  That endpoint's
+// lane processes both directed copies (i, j) and (j, i), so a vertex is a
+// partner only of its higher-ranked neighbours.
+__device__ __forceinline__ bool ranks_higher(int32_t di, int32_t dj, int32_t i, int32_t j) {
+    return di > dj || (di == dj && i < j);
+}
+
+// Walks the CSR segment by segment and calls body(e, row, col) per edge.
+template <typename Body>
+__device__ __forceinline__ void for_each_edge(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                                              const int32_t *__restrict__ seg_row, int64_t nnz, int32_t seg_len,
+                                              Body body) {
+    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
+        const int64_t e0 = s * seg_len;
+        const int64_t e1 = min(e0 + (int64_t)seg_len, nnz);
+        int32_t row = seg_row[s];
+        int64_t row_end = row_ptr[row + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            while (e >= row_end) {
+                ++row;
+                row_end = row_ptr[row + 1];
+            }
+            body(e, row, col_idx[e]);
+        }
+    }
+}
+
+__global__ void orient_flags_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                                    const int32_t *__restrict__ seg_row, const int32_t *__restrict__ deg,
+                                    int64_t nnz, int32_t seg_len, int32_t *__restrict__ flags) {
+    for_each_edge(row_ptr, col_idx, seg_row, nnz, seg_len, [&](int64_t e, int32_t i, int32_t j) {
+        flags[e] = ranks_higher(deg[i], deg[j], i, j) ? 1 : 0;
+    });
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[nnz] = 0;
+}
+
+__global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                                      const int32_t *__restrict__ seg_row, const int32_t *__restrict__ deg,
+                                      int64_t nnz, int32_t seg_len, const int32_t *__restrict__ pos,
+                                      int4 *__restrict__ ent) {
+    for_each_edge(row_ptr, col_idx, seg_row, nnz, seg_len, [&](int64_t e, int32_t i, int32_t j) {
+        if (!ranks_higher(deg[i], deg[j], i, j)) return;
+        const int32_t p = pos[e];
+        // index of the reverse copy (j, i): binary search for i in row j
+        int64_t lo = row_ptr[j], hi = row_ptr[j + 1] - 1;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (col_idx[mid] < i)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        ent[p] = make_int4(j, (int32_t)e, (int32_t)lo, 0);
+    });
+}
+
+__global__ void orient_rowptr_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ pos, int32_t n,
+                                     int64_t *__restrict__ act_row_ptr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride)
+        act_row_ptr[i] = pos[row_ptr[i]];
+}
+
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double warp_part[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -90,7 +158,7 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;   // valid in thread 0
 }
 
-// U^a summed over undirected edges (each counted once, from its i < j copy).
+// U^a summed over undirected edges, each counted once (from its i < j copy).
 // U^a(r) = alpha (r^2 / 2 + beta/2 ln(1 + r^2)), Eq. 2 with Table 1's attraction.
 __global__ void objective_edges_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                        const int32_t *__restrict__ seg_row, const float2 *__restrict__ pos,
@@ -120,6 +188,37 @@ __global__ void objective_edges_kernel(const int64_t *__restrict__ row_ptr, cons
                 const float r2 = fmaf(dx, dx, dy * dy);
                 part += kAlpha * (0.5f * r2 + 0.5f * kBeta * log1pf(r2));
             }
+        }
+        acc += (double)part;
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// U^a over an oriented list (each undirected edge once), walking its segments.
+__global__ void objective_oriented_kernel(const int64_t *__restrict__ row_ptr, const int4 *__restrict__ ent,
+                                          const int4 *__restrict__ seg, int64_t num_segs,
+                                          const float2 *__restrict__ pos, double *partial) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < num_segs; w += stride) {
+        const int4 sg = seg[w];
+        int32_t row = sg.z;
+        int64_t row_end = row_ptr[row + 1];
+        float2 yi = pos[row];
+        float part = 0.0f;
+        for (int64_t p = sg.x; p < sg.y; ++p) {
+            if (p >= row_end) {
+                do {
+                    ++row;
+                    row_end = row_ptr[row + 1];
+                } while (row_end <= p);
+                yi = pos[row];
+            }
+            const float2 yj = pos[ent[p].x];
+            const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+            const float r2 = fmaf(dx, dx, dy * dy);
+            part += kAlpha * (0.5f * r2 + 0.5f * kBeta * log1pf(r2));
         }
         acc += (double)part;
     }
@@ -218,10 +317,47 @@ cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, 
 }
 
 cudaError_t launch_objective_edges(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                   const float2 *pos, int64_t nnz, int32_t n, int32_t seg_len,
-                                   double *partial, int grid, cudaStream_t s) {
-    (void)n;
+                                   const float2 *pos, int64_t nnz, int32_t seg_len, double *partial, int grid,
+                                   cudaStream_t s) {
     objective_edges_kernel<<<grid, 256, 0, s>>>(row_ptr, col_idx, seg_row, pos, nnz, seg_len, partial);
+    return cudaGetLastError();
+}
+
+static int grid_for(int64_t items, int block) {
+    const int64_t want = (items + block - 1) / block;
+    return (int)(want < 65536 ? (want > 0 ? want : 1) : 65536);
+}
+
+cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
+                                const int32_t *deg, int64_t nnz, int32_t seg_len, int32_t *flags, cudaStream_t s) {
+    const int64_t segs = (nnz + seg_len - 1) / seg_len;
+    orient_flags_kernel<<<grid_for(segs, 256), 256, 0, s>>>(row_ptr, col_idx, seg_row, deg, nnz, seg_len, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in, int32_t *out, int64_t count,
+                               cudaStream_t s) {
+    return cub::DeviceScan::ExclusiveSum(temp, *temp_bytes, in, out, (int)count, s);
+}
+
+cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
+                                  const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
+                                  cudaStream_t s) {
+    const int64_t segs = (nnz + seg_len - 1) / seg_len;
+    orient_scatter_kernel<<<grid_for(segs, 256), 256, 0, s>>>(row_ptr, col_idx, seg_row, deg, nnz, seg_len, pos,
+                                                             ent);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int4 *seg, int64_t num_segs,
+                                      const float2 *pos, double *partial, int grid, cudaStream_t s) {
+    objective_oriented_kernel<<<grid, 256, 0, s>>>(row_ptr, ent, seg, num_segs, pos, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,
+                                 cudaStream_t s) {
+    orient_rowptr_kernel<<<grid_for((int64_t)n + 1, 256), 256, 0, s>>>(row_ptr, pos, n, act_row_ptr);
     return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "snap_internal.h"
 
@@ -59,12 +60,26 @@ __device__ __forceinline__ float2 repulsion_on_i(float dx, float dy) {
 
 // Position accesses that must see other SMs' writes: cached in L2 only.
 __device__ __forceinline__ float2 load_pos(const float2 *p) { return __ldcg(p); }
-__device__ __forceinline__ void store_pos(float2 *p, float2 v) { __stcg(p, v); }
+#ifndef SNAP_STORE_EXCH
+#define SNAP_STORE_EXCH 0
+#endif
+__device__ __forceinline__ void store_pos(float2 *p, float2 v) {
+#if SNAP_STORE_EXCH
+    unsigned long long bits;
+    memcpy(&bits, &v, 8);
+    atomicExch(reinterpret_cast<unsigned long long *>(p), bits);
+#else
+    __stcg(p, v);
+#endif
+}
 
 // The edge stream is read once per epoch: evict-first streaming loads.
 __device__ __forceinline__ int4 load_cols4(const int32_t *p) {
     return __ldcs(reinterpret_cast<const int4 *>(p));
 }
+
+// One oriented entry {j, index of (i, j), index of (j, i), unused}, streamed.
+__device__ __forceinline__ int4 load_entry(const int4 *p) { return __ldcs(p); }
 
 // int64 fixed point (2^-32) of one force component, clamped to +-2^20.
 __device__ __forceinline__ long long to_fixed(float v, uint32_t &flags) {

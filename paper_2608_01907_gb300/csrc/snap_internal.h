@@ -30,21 +30,6 @@ constexpr float kFixScale = 4294967296.0f;
 constexpr float kFixInv = 2.3283064365386963e-10f;   // 2^-32
 constexpr float kFixClamp = 1048576.0f;              // |term| <= 2^20 before scaling
 
-struct EpochArgs {
-    const int64_t *row_ptr;   // n + 1
-    const int32_t *col_idx;   // nnz (+ padding to a multiple of seg_len + 4)
-    const int32_t *seg_row;   // row containing edge seg * seg_len, per segment
-    float2 *pos;              // n
-    int64_t nnz;
-    int32_t n;
-    int32_t k;
-    int32_t seg_len;
-    uint32_t epoch;
-    uint64_t seed;
-    float eta;
-    uint32_t *status;
-};
-
 struct SyncArgs {
     const int64_t *row_ptr;
     const int32_t *col_idx;
@@ -60,11 +45,31 @@ struct SyncArgs {
     uint32_t *status;
 };
 
-cudaError_t launch_hogwild_epoch(const EpochArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+// Oriented bundle list: entry p of row i is {j, CSR index of (i, j), CSR
+// index of (j, i), 0} for a partner j ranked below i; segments are
+// {begin, end, first row, pieces}: whole rows, or one of `pieces` pieces of a
+// long row.
+struct OrientedArgs {
+    const int64_t *row_ptr;   // n + 1 offsets into ent
+    const int4 *ent;          // one entry per undirected edge
+    const int4 *seg;          // num_segs segments
+    float2 *pos;
+    int64_t num_segs;
+    int64_t perm_mul;         // segment order of this epoch: (perm_mul * w + perm_add) mod num_segs
+    int64_t perm_add;
+    int32_t n;
+    int32_t k;
+    uint32_t epoch;
+    uint64_t seed;
+    float eta;
+    uint32_t *status;
+};
+
+cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+int oriented_blocks_per_sm(int red_mode, int k, int block);
 cudaError_t launch_sync_chunk(const SyncArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_sync_apply(float2 *pos, long long *disp, int32_t n, float eta, float limit,
                               uint32_t *status, int grid, int block, cudaStream_t s);
-int hogwild_blocks_per_sm(int red_mode, int block);
 int sync_blocks_per_sm(int block);
 
 cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, int32_t seg_len,
@@ -72,10 +77,22 @@ cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, 
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags,
                                 cudaStream_t s);
+// Construction of the oriented bundle list (flags, exclusive scan, scatter, offsets).
+cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
+                                const int32_t *deg, int64_t nnz, int32_t seg_len, int32_t *flags, cudaStream_t s);
+cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in, int32_t *out, int64_t count,
+                               cudaStream_t s);
+cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
+                                  const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
+                                  cudaStream_t s);
+cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,
+                                 cudaStream_t s);
 // Objective partial sums (FP64), one per block, summed on the host in order.
 cudaError_t launch_objective_edges(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                   const float2 *pos, int64_t nnz, int32_t n, int32_t seg_len,
-                                   double *partial, int grid, cudaStream_t s);
+                                   const float2 *pos, int64_t nnz, int32_t seg_len, double *partial, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int4 *seg, int64_t num_segs,
+                                      const float2 *pos, double *partial, int grid, cudaStream_t s);
 cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n,
                                          double *partial, int grid, cudaStream_t s);
 cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, int32_t n,
