@@ -219,6 +219,42 @@ snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int3
                             int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
                             void *cuda_stream);
 
+/*
+ * snap_sync_epochs_noalloc -- the synchronous mode (SNAP_MODE_SYNC) for
+ * callers that cannot allocate device memory: code running inside a host
+ * framework that owns all device memory through its own pool or budget, or
+ * latency-critical code that must not pay for an allocation's implicit
+ * synchronisation.  The paper has no counterpart; it is a deployment variant
+ * of the same computation.
+ *
+ * Allocates nothing: no cudaMalloc/cudaFree and no allocating library call.
+ * The per-vertex int64 displacement scratch lives in a fixed device array
+ * inside the library, sized for at most 262,144 vertices (4 MiB, present on
+ * every GPU that loads the library until the process exits).
+ *
+ *   row_ptr, col_idx  DEVICE, caller-owned, the symmetric CSR contract of
+ *                     snap_layout_create (not re-validated; a column outside
+ *                     [0, n) is skipped and reported as INVALID_ARG).
+ *   n                 1 <= n <= 262,144, else INVALID_ARG.
+ *   positions         device, n x 2 float32, updated in place.
+ *   epoch_begin, epochs, neg_samples, schedule, seed
+ *                     as snap_layout_epochs.
+ *   substeps, cap     as snap_options.sync_substeps / sync_cap.
+ *
+ * The result equals snap_layout_epochs on a SNAP_MODE_SYNC handle with the
+ * same substeps and cap (default 32-edge segments).  The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls in the process share
+ * the scratch, which keeps the last call's contents (each call clears it
+ * first): calls that overlap on the GPU -- other streams, other host
+ * threads -- race and must be serialised by the caller.  Waits for the
+ * stream before returning.  Errors: INVALID_ARG, CUDA, NUMERIC.
+ */
+snap_status snap_sync_epochs_noalloc(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                                     float *positions, int32_t epoch_begin, int32_t epochs,
+                                     int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                                     int32_t substeps, float cap, void *cuda_stream);
+
 /* Message for the last non-OK status returned on this host thread. */
 const char *snap_last_error(void);
 

@@ -21,7 +21,7 @@ __all__ = [
     "SAMPLER_UNIFORM", "SAMPLER_DEGREE", "SAMPLER_WEIGHTS", "build", "library_path", "load_library",
     "snap_options_default", "snap_layout_create", "snap_layout_epochs", "snap_layout_objective",
     "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
-    "snap_layout_run", "snap_last_error", "Layout", "linear_schedule",
+    "snap_layout_run", "snap_last_error", "Layout", "linear_schedule", "snap_sync_epochs_noalloc",
 ]
 
 MODE_HOGWILD, MODE_HOGWILD_RED, MODE_SYNC = 0, 1, 2
@@ -93,6 +93,8 @@ def load_library():
     lib.snap_graph_reorder.restype = st
     lib.snap_layout_run.argtypes = [P, P, i32, P, P, i32, i32, P, u64, P]
     lib.snap_layout_run.restype = st
+    lib.snap_sync_epochs_noalloc.argtypes = [P, P, i32, P, i32, i32, i32, P, u64, i32, ctypes.c_float, P]
+    lib.snap_sync_epochs_noalloc.restype = st
     lib.snap_last_error.argtypes = []
     lib.snap_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -229,6 +231,27 @@ def snap_layout_run(row_ptr, col_idx, positions_host, epochs: int, neg_samples: 
     _check(load_library().snap_layout_run(_ptr(rp), _ptr(ci), n, ctypes.byref(opts) if opts is not None else None,
                                           pp, epochs, neg_samples, ctypes.byref(schedule), seed, _stream(stream)))
     return positions_host
+
+
+def snap_sync_epochs_noalloc(row_ptr, col_idx, positions, epoch_begin: int, epochs: int, neg_samples: int,
+                             schedule: SnapSchedule, seed: int, substeps: int = 1, cap: float = 0.0,
+                             stream=None) -> None:
+    """Synchronous epochs without any device allocation (see the C header).
+
+    row_ptr (int64), col_idx (int32) and positions ((n, 2) float32) are CUDA
+    tensors the caller owns; n is positions.shape[0] (at most 262,144)."""
+    import torch
+    for t, dt in ((row_ptr, torch.int64), (col_idx, torch.int32)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise TypeError("row_ptr / col_idx must be contiguous CUDA tensors (int64 / int32)")
+    p = _device_positions(positions)
+    n = int(positions.shape[0])
+    if row_ptr.numel() != n + 1:
+        raise ValueError("row_ptr must have n + 1 entries")
+    _check(load_library().snap_sync_epochs_noalloc(ctypes.c_void_p(row_ptr.data_ptr()),
+                                                   ctypes.c_void_p(col_idx.data_ptr()), n, p, epoch_begin, epochs,
+                                                   neg_samples, ctypes.byref(schedule), seed, substeps, cap,
+                                                   _stream(stream)))
 
 
 @dataclass
