@@ -53,6 +53,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-sample-edges", type=int, default=12_000_000)
+    p.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve"],
+                   help="rmat: the 4M/34M headline; batch: many small SBM graphs, batched vs one launch per "
+                        "graph; serve: Poisson layout requests, continuous batching vs one job at a time")
+    p.add_argument("--serve-seconds", type=float, default=5.0)
+    p.add_argument("--serve-rate", type=float, default=200.0)
+    p.add_argument("--batch-graphs", type=int, default=4096)
+    p.add_argument("--per-graph-sample", type=int, default=512)
     return p.parse_args()
 
 
@@ -398,6 +405,191 @@ def run_snap(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def load_batch(count, seed):
+    """4096 SBM graphs (n log-uniform 100..20,000, 4..32 communities, mean
+    degree 6..20, mixing 0.1) as one disjoint union; cached on local disk."""
+    import paper_2608_01907_gb300 as snap
+    from synth import batch_sbm_graphs
+    cache = os.path.join(tempfile.gettempdir(), "snap_bench_cache")
+    os.makedirs(cache, exist_ok=True)
+    path = os.path.join(cache, f"batch_sbm_{count}_s{seed}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return z["row_ptr"], z["col_idx"], z["offsets"]
+    graphs = batch_sbm_graphs(count=count, seed=seed)
+    rp, ci, offs = snap.batch_union([(g.row_ptr, g.col_idx) for g in graphs])
+    tmp = path + f".{os.getpid()}.npz"
+    np.savez(tmp, row_ptr=rp, col_idx=ci, offsets=offs)
+    os.replace(tmp, path)
+    return rp, ci, offs
+
+
+def run_batch(args, rank, world, local_rank):
+    """Config 4: many small graphs in one handle against one handle (and one
+    launch per epoch) per graph.  One step = the 30-epoch layout of all
+    graphs."""
+    import torch
+    import paper_2608_01907_gb300 as snap
+    torch.cuda.set_device(local_rank)
+    rp, ci, offs = load_batch(args.batch_graphs, args.seed)
+    n = int(offs[-1])
+    nnz = int(rp[-1])
+    k = args.k
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=EPOCHS)
+    stream = torch.cuda.current_stream()
+    Y0 = initial_positions(n, args.seed)
+    Y0_d = torch.from_numpy(Y0).cuda()
+    Y = torch.empty_like(Y0_d)
+    h = snap.snap_layout_create_batch(rp, ci, offs, None, stream)
+
+    def step():
+        Y.copy_(Y0_d)
+        snap.snap_layout_epochs(h, Y, 0, EPOCHS, k, sched, args.seed, stream)
+
+    for _ in range(args.warmup):
+        step()
+    snap.snap_layout_check(h, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    snap.snap_layout_check(h, stream)
+    ms = e0.elapsed_time(e1) / args.steps
+    updates = EPOCHS * nnz * (1 + k)
+    snap.snap_layout_destroy(h)
+
+    # one graph per handle and per launch, on a seeded sample of the graphs
+    rng = np.random.default_rng(args.seed)
+    sample = np.sort(rng.choice(offs.size - 1, min(args.per_graph_sample, offs.size - 1), replace=False))
+    handles = []
+    for q in sample:
+        a, b = int(offs[q]), int(offs[q + 1])
+        sub_rp = rp[a:b + 1] - rp[a]
+        sub_ci = ci[rp[a]:rp[b]] - a
+        handles.append((a, b, int(sub_rp[-1]), snap.snap_layout_create(sub_rp, sub_ci, None, b - a, None, stream)))
+    views = [Y[a:b] for a, b, _, _ in handles]
+    for (a, b, _, hh), v in zip(handles, views):      # warm-up
+        v.copy_(Y0_d[a:b])
+        snap.snap_layout_epochs(hh, v, 0, 1, k, sched, args.seed, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for (a, b, _, hh), v in zip(handles, views):
+        v.copy_(Y0_d[a:b])
+        for t in range(EPOCHS):
+            snap.snap_layout_epochs(hh, v, t, 1, k, sched, args.seed, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pg = e0.elapsed_time(e1)
+    upd_pg = EPOCHS * sum(m for _, _, m, _ in handles) * (1 + k)
+    for _, _, _, hh in handles:
+        snap.snap_layout_destroy(hh)
+    line = {"metric": "batched layouts: pair updates/s and s per batch (30 epochs)", "value": updates / (ms / 1e3),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch-sbm-{offs.size - 1}-graphs-k{k}-{EPOCHS}ep", "graphs": int(offs.size - 1),
+                       "n_total": n, "undirected_edges": nnz // 2, "mode": "hogwild"},
+            "one_graph_per_launch": {"updates_per_s": upd_pg / (ms_pg / 1e3), "graphs_timed": len(handles),
+                                     "launches": len(handles) * EPOCHS, "ms": ms_pg},
+            "speedup_vs_one_graph_per_launch": (updates / (ms / 1e3)) / (upd_pg / (ms_pg / 1e3)),
+            "gpu_launches": args.steps * EPOCHS, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, rank, world, local_rank):
+    """Config 5: layout requests arriving as a Poisson stream (mean 200/s) over
+    R-MAT and planted-partition graphs with |E| log-uniform in [1k, 2M];
+    continuous batching (LayoutServer) against the plain loop (one job at a
+    time, first come first served) on the same arrival schedule."""
+    import torch
+    import paper_2608_01907_gb300 as snap
+    from paper_2608_01907_gb300.serve import Job, LayoutServer, run_sequential
+    from synth import serving_graph_pool
+    torch.cuda.set_device(local_rank)
+    pool = serving_graph_pool(48, seed=args.seed)
+    rng = np.random.default_rng(args.seed)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        arrivals.append(t)
+    picks = rng.integers(0, len(pool), len(arrivals))
+
+    def make_jobs():
+        return [Job(q, pool[g].row_ptr, pool[g].col_idx, initial_positions(pool[g].n, 1000 + q), seed=q)
+                for q, g in enumerate(picks)]
+
+    k = args.k
+    # warm-up: a few jobs through both paths (not timed)
+    warm = [Job(-1 - q, pool[q].row_ptr, pool[q].col_idx, initial_positions(pool[q].n, q), seed=q) for q in range(4)]
+    server = LayoutServer(hbm_budget=int(0.5 * torch.cuda.mem_get_info()[0]), max_jobs=1024, epochs=EPOCHS,
+                          neg_samples=k, eta0=1.0)
+    for j in warm:
+        server.submit(j)
+    server.drain()
+    run_sequential(warm[:2], epochs=EPOCHS, neg_samples=k)
+    torch.cuda.synchronize()
+
+    def served():
+        jobs = make_jobs()
+        server.done.clear()
+        server.updates = 0
+        t0 = time.perf_counter()
+        nxt = 0
+        while nxt < len(jobs) or not server.idle():
+            now = time.perf_counter() - t0
+            while nxt < len(jobs) and arrivals[nxt] <= now:
+                server.submit(jobs[nxt])
+                jobs[nxt].submitted = t0 + arrivals[nxt]
+                nxt += 1
+            if server.idle():
+                if nxt < len(jobs):
+                    time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
+                continue
+            server.tick()
+        server.multi.check(server.stream)
+        return jobs, t0
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    jobs_s, t0_s = served()
+    clk = clocks.stop()
+    server.close()
+    jobs_p = make_jobs()
+    t0_p = time.perf_counter()
+    run_sequential(jobs_p, epochs=EPOCHS, neg_samples=k, arrivals=arrivals)
+
+    def summary(jobs, t0):
+        lat = np.array([j.finished - j.submitted for j in jobs])
+        upd = sum(j.nnz * (1 + k) * EPOCHS for j in jobs)
+        span = max(j.finished for j in jobs) - t0
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "updates_per_s": upd / span, "makespan_s": span}
+
+    srv, seq = summary(jobs_s, t0_s), summary(jobs_p, t0_p)
+    finite = all(np.all(np.isfinite(j.positions)) for j in jobs_s)
+    line = {"metric": "served layout requests: p50/p99 latency and pair updates/s", "value": srv["updates_per_s"],
+            "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve-poisson{args.serve_rate:g}-{len(arrivals)}jobs-{EPOCHS}ep-k{k}",
+                       "jobs": len(arrivals), "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+                       "graph_pool": "48 graphs: R-MAT / 8-community planted partition, |E| log-uniform 1k-2M",
+                       "mode": "hogwild"},
+            "continuous_batching": srv, "one_job_at_a_time": seq,
+            "p99_speedup": seq["p99_s"] / srv["p99_s"], "throughput_ratio": srv["updates_per_s"] / seq["updates_per_s"],
+            "all_finite": finite, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -405,6 +597,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        run_batch(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local_rank)
     else:
         run_snap(args, rank, world, local_rank)
 

@@ -104,10 +104,19 @@ typedef struct {
     float sync_cap;           /* > 0: clip each node's sync step to cap*eta_t/eta0 */
     int32_t segment_edges;    /* work per lane segment, a multiple of 4 in [4, 4096]: oriented entries
                                  (2 directed edges each) in the HOGWILD modes, directed edges in SYNC;
-                                 0 = default (HOGWILD: 32 for large graphs, 128 for small ones;
-                                 SYNC: 32) */
+                                 0 = default (HOGWILD: 4; SYNC: 32) */
     int32_t block_threads;    /* threads per block; 0 = default (256) */
+    int32_t flags;            /* SNAP_FLAG_* bits */
+    float max_inflight;       /* HOGWILD: at most this share of the graph's entries in flight at once
+                                 (lanes = share x entries); 0 = default 0.01.  Concurrent updates of one
+                                 vertex degrade Hogwild quality on small graphs */
 } snap_options;
+
+/* snap_options.flags: capture the launches of a snap_layout_epochs call with
+ * epochs > 1 into a CUDA graph on first use and replay it on later calls
+ * with the same positions pointer, epoch range, k, schedule and seed (up to 4
+ * graphs are cached per handle). */
+#define SNAP_FLAG_CUDA_GRAPH 1
 
 /* Fill *opts with the defaults (HOGWILD, UNIFORM, S = 1, no cap). */
 void snap_options_default(snap_options *opts);
@@ -136,6 +145,30 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx,
                                const int32_t *degrees, int32_t n,
                                const snap_options *opts, void *cuda_stream,
                                snap_layout_t *out);
+
+/*
+ * snap_layout_create_batch -- many graphs laid out together, in the same
+ * launches (the paper lays out one graph at a time; batching is a
+ * deployment form of the same method).
+ *
+ *   row_ptr, col_idx, n  host, the disjoint union of the graphs as one CSR
+ *                        with the contract of snap_layout_create; graph g owns
+ *                        vertices [graph_offsets[g], graph_offsets[g+1]) and
+ *                        no edge may join two graphs (INVALID_ARG).
+ *   graph_offsets        host, num_graphs + 1 int32, strictly increasing,
+ *                        from 0 to n.
+ *
+ * On the returned handle snap_layout_epochs lays out every graph at once with
+ * the call's schedule and seed; each graph draws its negatives from its own
+ * vertices, and its random words use its own edge indices (offset from the
+ * graph's first edge), so every graph draws exactly the numbers it would draw
+ * in a handle of its own: in SNAP_MODE_SYNC with sync_substeps = 1 the result
+ * equals the one-graph layouts bit for bit.  snap_layout_objective returns
+ * the sum over graphs of their objectives (exact = 1 only).
+ */
+snap_status snap_layout_create_batch(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                                     const int32_t *graph_offsets, int32_t num_graphs,
+                                     const snap_options *opts, void *cuda_stream, snap_layout_t *out);
 
 /*
  * snap_layout_epochs -- run epochs [epoch_begin, epoch_begin + epochs) of
@@ -188,7 +221,27 @@ snap_status snap_layout_check(snap_layout_t h, void *cuda_stream);
 /* Device bytes held by the handle (CSR, tables, scratch; positions excluded). */
 int64_t snap_layout_device_bytes(snap_layout_t h);
 
-/* Release the handle and its device memory.  NULL is ignored. */
+/*
+ * snap_layout_autotune -- choose the segment size (bundle entries per lane)
+ * and the block size of a HOGWILD handle by timing epochs.  Candidates are
+ * 4, 8, 16, 32 entries x 128/256 threads, all under the handle's
+ * max_inflight bound (max_inflight here is unused and kept for the ABI).  The
+ * chosen configuration stays on the handle.
+ *
+ *   scratch_positions  device, n x 2 float32; overwritten (3 epochs per
+ *                      candidate at a constant step).
+ *   chosen_segment, chosen_block, chosen_ms   host outputs (nullable).
+ * Synchronises the stream.  Errors: INVALID_ARG, NOT_SUPPORTED (SYNC), CUDA.
+ */
+snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int32_t neg_samples,
+                                 double max_inflight, int32_t *chosen_segment, int32_t *chosen_block,
+                                 double *chosen_ms, void *cuda_stream);
+
+/* Release the handle and its device memory.  NULL is ignored.  Does not
+ * synchronise: the memory is freed stream-ordered after the work of the
+ * handle's latest call (all work on a handle is assumed to be ordered on the
+ * stream of its latest call).  The handle's memory is allocated
+ * stream-ordered on the stream given to create. */
 void snap_layout_destroy(snap_layout_t h);
 
 /*
@@ -254,6 +307,37 @@ snap_status snap_sync_epochs_noalloc(const int64_t *row_ptr, const int32_t *col_
                                      float *positions, int32_t epoch_begin, int32_t epochs,
                                      int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
                                      int32_t substeps, float cap, void *cuda_stream);
+
+/*
+ * Multi-handle epochs -- continuous batching of independent layouts.  The
+ * paper lays out one graph at a time; this runs one epoch of several layouts
+ * (jobs) in ONE kernel launch, each job at its own epoch index, step size and
+ * seed, so jobs that arrive while others run can join at the next launch and
+ * leave when their schedule ends.  Each job's random words are those of its
+ * own handle, so its result is independent of the other jobs except through
+ * race timing (and identical when each job is processed by a single lane,
+ * i.e. segment_edges >= its entries).
+ *
+ * snap_multi_create  allocates a job table for up to max_jobs jobs per call.
+ * snap_multi_epoch   enqueues epoch epochs[q] of job q for q < count:
+ *     handles[q]     single-graph handle in SNAP_MODE_HOGWILD or
+ *                    SNAP_MODE_HOGWILD_RED (all the same mode), else
+ *                    NOT_SUPPORTED / INVALID_ARG;
+ *     positions[q]   device pointer to that job's n x 2 float32 positions;
+ *     schedules[q], seeds[q]  as in snap_layout_epochs.
+ *   Asynchronous; it waits only until the previous call's job table has
+ *   reached the device.  Jobs without edges are skipped.
+ * snap_multi_check   waits for the stream; NUMERIC if a position became
+ *                    non-finite in any job since the last check.
+ */
+typedef struct snap_multi snap_multi;
+typedef snap_multi *snap_multi_t;
+snap_status snap_multi_create(int32_t max_jobs, snap_multi_t *out);
+snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float *const *positions,
+                             const int32_t *epochs, const snap_schedule *schedules, const uint64_t *seeds,
+                             int32_t count, int32_t neg_samples, void *cuda_stream);
+snap_status snap_multi_check(snap_multi_t m, void *cuda_stream);
+void snap_multi_destroy(snap_multi_t m);
 
 /* Message for the last non-OK status returned on this host thread. */
 const char *snap_last_error(void);

@@ -22,6 +22,7 @@ __all__ = [
     "snap_options_default", "snap_layout_create", "snap_layout_epochs", "snap_layout_objective",
     "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
     "snap_layout_run", "snap_last_error", "Layout", "linear_schedule", "snap_sync_epochs_noalloc",
+    "snap_layout_create_batch", "batch_union", "snap_layout_autotune", "MultiEpoch",
 ]
 
 MODE_HOGWILD, MODE_HOGWILD_RED, MODE_SYNC = 0, 1, 2
@@ -45,7 +46,11 @@ class SnapOptions(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sampler", ctypes.c_int32),
                 ("node_weights", ctypes.c_void_p), ("sync_substeps", ctypes.c_int32),
                 ("sync_cap", ctypes.c_float), ("segment_edges", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("max_inflight", ctypes.c_float)]
+
+
+FLAG_CUDA_GRAPH = 1
 
 
 def linear_schedule(eta0: float = 1.0, total_epochs: int = 30, eta_min: float | None = None,
@@ -79,12 +84,16 @@ def load_library():
     lib.snap_options_default.restype = None
     lib.snap_layout_create.argtypes = [P, P, P, i32, P, P, P]
     lib.snap_layout_create.restype = st
+    lib.snap_layout_create_batch.argtypes = [P, P, i32, P, i32, P, P, P]
+    lib.snap_layout_create_batch.restype = st
     lib.snap_layout_epochs.argtypes = [P, P, i32, i32, i32, P, u64, P]
     lib.snap_layout_epochs.restype = st
     lib.snap_layout_objective.argtypes = [P, P, i32, i32, i64, u64, P, P, P, P]
     lib.snap_layout_objective.restype = st
     lib.snap_layout_check.argtypes = [P, P]
     lib.snap_layout_check.restype = st
+    lib.snap_layout_autotune.argtypes = [P, P, i32, f64, P, P, P, P]
+    lib.snap_layout_autotune.restype = st
     lib.snap_layout_device_bytes.argtypes = [P]
     lib.snap_layout_device_bytes.restype = i64
     lib.snap_layout_destroy.argtypes = [P]
@@ -95,6 +104,14 @@ def load_library():
     lib.snap_layout_run.restype = st
     lib.snap_sync_epochs_noalloc.argtypes = [P, P, i32, P, i32, i32, i32, P, u64, i32, ctypes.c_float, P]
     lib.snap_sync_epochs_noalloc.restype = st
+    lib.snap_multi_create.argtypes = [i32, P]
+    lib.snap_multi_create.restype = st
+    lib.snap_multi_epoch.argtypes = [P, P, P, P, P, P, i32, i32, P]
+    lib.snap_multi_epoch.restype = st
+    lib.snap_multi_check.argtypes = [P, P]
+    lib.snap_multi_check.restype = st
+    lib.snap_multi_destroy.argtypes = [P]
+    lib.snap_multi_destroy.restype = None
     lib.snap_last_error.argtypes = []
     lib.snap_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -147,10 +164,13 @@ def snap_options_default() -> SnapOptions:
 
 
 def make_options(mode: int = MODE_HOGWILD, sync_substeps: int = 1, sync_cap: float = 0.0,
-                 segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM) -> SnapOptions:
+                 segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM,
+                 cuda_graph: bool = False, max_inflight: float = 0.0) -> SnapOptions:
     o = snap_options_default()
     o.mode, o.sync_substeps, o.sync_cap = mode, sync_substeps, sync_cap
     o.segment_edges, o.block_threads, o.sampler = segment_edges, block_threads, sampler
+    o.flags = FLAG_CUDA_GRAPH if cuda_graph else 0
+    o.max_inflight = max_inflight
     return o
 
 
@@ -164,6 +184,19 @@ def snap_layout_create(row_ptr, col_idx, degrees=None, n: int | None = None, opt
     _check(load_library().snap_layout_create(_ptr(rp), _ptr(ci), _ptr(dg), n,
                                              ctypes.byref(opts) if opts is not None else None,
                                              _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def snap_layout_create_batch(row_ptr, col_idx, graph_offsets, opts: SnapOptions | None = None,
+                             stream=None) -> ctypes.c_void_p:
+    """Handle over the disjoint union of several graphs (see the C header)."""
+    rp = _host(row_ptr, np.int64)
+    ci = _host(col_idx, np.int32)
+    go = _host(graph_offsets, np.int32)
+    out = ctypes.c_void_p()
+    _check(load_library().snap_layout_create_batch(_ptr(rp), _ptr(ci), rp.size - 1, _ptr(go), go.size - 1,
+                                                   ctypes.byref(opts) if opts is not None else None,
+                                                   _stream(stream), ctypes.byref(out)))
     return out
 
 
@@ -184,6 +217,15 @@ def snap_layout_objective(h, positions, neg_samples: int, exact: bool = True, pa
 
 def snap_layout_check(h, stream=None) -> None:
     _check(load_library().snap_layout_check(h, _stream(stream)))
+
+
+def snap_layout_autotune(h, scratch_positions, neg_samples: int, max_inflight: float = 0.0, stream=None):
+    """Returns (segment entries, block threads, ms per epoch) chosen for the handle."""
+    seg, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load_library().snap_layout_autotune(h, _device_positions(scratch_positions), neg_samples, max_inflight,
+                                               ctypes.byref(seg), ctypes.byref(blk), ctypes.byref(ms),
+                                               _stream(stream)))
+    return seg.value, blk.value, ms.value
 
 
 def snap_layout_device_bytes(h) -> int:
@@ -233,6 +275,24 @@ def snap_layout_run(row_ptr, col_idx, positions_host, epochs: int, neg_samples: 
     return positions_host
 
 
+def batch_union(graphs):
+    """Disjoint union of (row_ptr, col_idx) CSRs: returns (row_ptr, col_idx,
+    graph_offsets) with graph g's vertices relabelled by its offset."""
+    offs = [0]
+    rps, cis = [], []
+    ebase = 0
+    for rp, ci in graphs:
+        rp = np.asarray(rp, dtype=np.int64)
+        ci = np.asarray(ci, dtype=np.int32)
+        rps.append(rp[:-1] + ebase)
+        cis.append(ci + offs[-1])
+        ebase += int(rp[-1])
+        offs.append(offs[-1] + rp.size - 1)
+    row_ptr = np.concatenate(rps + [np.array([ebase], dtype=np.int64)])
+    col_idx = np.concatenate(cis) if cis else np.zeros(0, np.int32)
+    return row_ptr, col_idx.astype(np.int32), np.array(offs, dtype=np.int32)
+
+
 def snap_sync_epochs_noalloc(row_ptr, col_idx, positions, epoch_begin: int, epochs: int, neg_samples: int,
                              schedule: SnapSchedule, seed: int, substeps: int = 1, cap: float = 0.0,
                              stream=None) -> None:
@@ -252,6 +312,49 @@ def snap_sync_epochs_noalloc(row_ptr, col_idx, positions, epoch_begin: int, epoc
                                                    ctypes.c_void_p(col_idx.data_ptr()), n, p, epoch_begin, epochs,
                                                    neg_samples, ctypes.byref(schedule), seed, substeps, cap,
                                                    _stream(stream)))
+
+
+class MultiEpoch:
+    """One kernel launch per call running one epoch of several single-graph
+    HOGWILD handles, each at its own epoch, schedule and seed (continuous
+    batching; see snap_multi_* in the C header)."""
+
+    def __init__(self, max_jobs: int = 1024):
+        self.handle = ctypes.c_void_p()
+        self.max_jobs = max_jobs
+        _check(load_library().snap_multi_create(max_jobs, ctypes.byref(self.handle)))
+        self._h = (ctypes.c_void_p * max_jobs)()
+        self._p = (ctypes.c_void_p * max_jobs)()
+        self._e = (ctypes.c_int32 * max_jobs)()
+        self._s = (SnapSchedule * max_jobs)()
+        self._seed = (ctypes.c_uint64 * max_jobs)()
+
+    def epoch(self, jobs, neg_samples: int, stream=None) -> None:
+        """jobs: iterable of (handle, positions tensor, epoch, SnapSchedule, seed)."""
+        q = 0
+        for h, pos, ep, sched, seed in jobs:
+            self._h[q] = h.value if isinstance(h, ctypes.c_void_p) else h
+            self._p[q] = pos.data_ptr()
+            self._e[q] = ep
+            self._s[q] = sched
+            self._seed[q] = seed
+            q += 1
+        _check(load_library().snap_multi_epoch(self.handle, self._h, self._p, self._e, self._s, self._seed, q,
+                                               neg_samples, _stream(stream)))
+
+    def check(self, stream=None) -> None:
+        _check(load_library().snap_multi_check(self.handle, _stream(stream)))
+
+    def close(self) -> None:
+        if self.handle:
+            load_library().snap_multi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass

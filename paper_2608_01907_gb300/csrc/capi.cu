@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -53,14 +54,74 @@ struct AllocCounter {
 thread_local AllocCounter g_alloc;
 thread_local bool g_in_run = false;
 
-cudaError_t dev_alloc(AllocCounter &ac, void **p, size_t bytes) {
+// Handle memory is stream-ordered (cudaMallocAsync on the creating stream,
+// cudaFreeAsync when released), so creating and destroying handles never
+// synchronises the device -- a server admits and retires layouts while other
+// layouts keep running.
+cudaError_t dev_alloc(AllocCounter &ac, void **p, size_t bytes, cudaStream_t stream) {
     ++ac.count;
     if (ac.fail_at > 0 && ac.count == ac.fail_at) {
         *p = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    return cudaMallocAsync(p, bytes < 16 ? 16 : bytes, stream);
 }
+
+// One non-blocking stream per device on which released memory is freed,
+// after waiting for the last work that used it.
+cudaStream_t free_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
+// Pinned 16-byte status slots, handed out to handles and reused; the pool's
+// pages live until the process exits.
+struct StatusSlots {
+    std::mutex mu;
+    std::vector<uint32_t *> free_slots;
+    std::vector<std::pair<uint32_t *, cudaEvent_t>> quarantine;   // read-back may be in flight
+
+    uint32_t *take() {
+        std::lock_guard<std::mutex> lock(mu);
+        for (size_t q = 0; q < quarantine.size();) {
+            if (cudaEventQuery(quarantine[q].second) == cudaSuccess) {
+                cudaEventDestroy(quarantine[q].second);
+                free_slots.push_back(quarantine[q].first);
+                quarantine[q] = quarantine.back();
+                quarantine.pop_back();
+            } else {
+                ++q;
+            }
+        }
+        cudaGetLastError();
+        if (free_slots.empty()) {
+            uint32_t *page = nullptr;
+            if (cudaMallocHost((void **)&page, 4096 * 4 * sizeof(uint32_t)) != cudaSuccess) return nullptr;
+            for (int q = 4095; q >= 0; --q) free_slots.push_back(page + 4 * q);
+        }
+        uint32_t *slot = free_slots.back();
+        free_slots.pop_back();
+        return slot;
+    }
+
+    // `pending` (or nullptr) completes once no copy into the slot is in flight;
+    // the pool then owns and destroys it.
+    void give(uint32_t *slot, cudaEvent_t pending) {
+        if (!slot) return;
+        std::lock_guard<std::mutex> lock(mu);
+        if (pending)
+            quarantine.emplace_back(slot, pending);
+        else
+            free_slots.push_back(slot);
+    }
+};
+
+StatusSlots g_status_slots;
 
 // SplitMix64 finaliser (Steele, Lea, Flood 2014): the per-epoch offset of
 // the segment order.
@@ -86,6 +147,14 @@ namespace snap {
 snap_status reorder_fail(snap_status st, const char *msg) { return fail(st, "%s", msg); }
 }  // namespace snap
 
+struct CapturedEpochs {
+    const float *pos;
+    int32_t epoch_begin, epochs, k;
+    uint64_t seed;
+    snap_schedule sched;
+    cudaGraphExec_t exec;
+};
+
 struct snap_layout {
     int32_t n = 0;
     int64_t nnz = 0;
@@ -107,6 +176,17 @@ struct snap_layout {
     int64_t *d_act_row_ptr = nullptr;
     int4 *d_act_ent = nullptr;
     int4 *d_act_seg = nullptr;
+    size_t act_seg_capacity = 0;
+    std::vector<int64_t> act_rp_host;   // host copy of the oriented row offsets (for repacking)
+    // batch of graphs (num_graphs > 1): graph of every vertex and per-graph table
+    int32_t num_graphs = 1;
+    std::vector<int32_t> graph_offsets;   // num_graphs + 1 vertex offsets
+    int32_t *d_node_graph = nullptr;
+    GraphInfo *d_graphs = nullptr;
+    std::vector<GraphInfo> h_graphs;
+    bool graphs_set = false;
+    snap_schedule graphs_sched{};
+    uint64_t graphs_seed = 0;
     uint32_t *d_status = nullptr;   // [0] fault bits, [1] validation bits
     double *d_partial = nullptr;    // 2 * kObjGrid
     uint32_t *h_status = nullptr;   // pinned mirror of d_status[0]
@@ -117,11 +197,34 @@ struct snap_layout {
     int grid_oriented[2][5] = {{0}};   // [red][min(k, 4)], filled on first use
     std::vector<int64_t> chunk_edges;   // S + 1 edge offsets of the sync chunks
     int64_t device_bytes = 0;
+    // CUDA graphs of captured epoch sequences (SNAP_FLAG_CUDA_GRAPH)
+    cudaStream_t capture_stream = nullptr;
+    std::vector<CapturedEpochs> captured;
+
+    // Work that last used the handle's memory: the creating stream until the
+    // first call, then the stream of the latest call.
+    cudaStream_t alloc_stream = nullptr;
+    cudaEvent_t last_use = nullptr;
+
+    void mark_use(cudaStream_t s) {
+        if (last_use) cudaEventRecord(last_use, s);
+    }
+
+    void free_async(void *p) {
+        if (!p) return;
+        cudaStream_t fs = free_stream();
+        if (fs && last_use) {
+            cudaStreamWaitEvent(fs, last_use, 0);
+            cudaFreeAsync(p, fs);
+        } else {
+            cudaFreeAsync(p, alloc_stream);
+        }
+    }
 
     void release_csr() {
-        cudaFree(d_row_ptr);
-        cudaFree(d_col);
-        cudaFree(d_seg_row);
+        free_async(d_row_ptr);
+        free_async(d_col);
+        free_async(d_seg_row);
         d_row_ptr = nullptr;
         d_col = nullptr;
         d_seg_row = nullptr;
@@ -129,18 +232,34 @@ struct snap_layout {
 
     void release() {
         release_csr();
-        cudaFree(d_act_row_ptr);
-        cudaFree(d_act_ent);
-        cudaFree(d_act_seg);
+        free_async(d_act_row_ptr);
+        free_async(d_act_ent);
+        free_async(d_act_seg);
+        free_async(d_node_graph);
+        free_async(d_graphs);
+        d_node_graph = nullptr;
+        d_graphs = nullptr;
         d_act_row_ptr = nullptr;
         d_act_ent = nullptr;
         d_act_seg = nullptr;
-        cudaFree(d_deg);
-        cudaFree(d_disp);
-        cudaFree(d_status);
-        cudaFree(d_partial);
-        if (h_status) cudaFreeHost(h_status);
+        free_async(d_deg);
+        free_async(d_disp);
+        free_async(d_status);
+        free_async(d_partial);
+        if (status_pending && status_event) {
+            g_status_slots.give(h_status, status_event);   // the pool destroys the event
+            status_event = nullptr;
+        } else {
+            g_status_slots.give(h_status, nullptr);
+        }
+        status_pending = false;
+        for (const CapturedEpochs &c : captured) cudaGraphExecDestroy(c.exec);
+        captured.clear();
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+        capture_stream = nullptr;
         if (status_event) cudaEventDestroy(status_event);
+        if (last_use) cudaEventDestroy(last_use);
+        last_use = nullptr;
         d_deg = nullptr;
         d_disp = nullptr;
         d_status = nullptr;
@@ -161,16 +280,22 @@ static int64_t gcd64(int64_t a, int64_t b) {
 
 // Segments of the oriented list: whole rows packed greedily up to `target`
 // entries; a row longer than `target` is cut into equal pieces.
-static void pack_segments(const std::vector<int64_t> &rp, int32_t target, std::vector<int4> &out) {
+static void pack_segments(const std::vector<int64_t> &rp, int32_t target, const std::vector<int32_t> &graph_offsets,
+                          std::vector<int4> &out) {
     out.clear();
     const int32_t n = (int32_t)rp.size() - 1;
     int64_t open_begin = -1, open_end = 0;
     int32_t open_row = 0;
+    size_t next_graph = 1;   // segments never span two graphs of a batch
     auto close = [&]() {
         if (open_begin >= 0) out.push_back(make_int4((int)open_begin, (int)open_end, open_row, 1));
         open_begin = -1;
     };
     for (int32_t i = 0; i < n; ++i) {
+        while (next_graph < graph_offsets.size() && graph_offsets[next_graph] <= i) {
+            close();
+            ++next_graph;
+        }
         const int64_t len = rp[(size_t)i + 1] - rp[(size_t)i];
         if (len == 0) continue;
         if (len > target) {
@@ -193,6 +318,40 @@ static void pack_segments(const std::vector<int64_t> &rp, int32_t target, std::v
     close();
 }
 
+// (Re)packs the oriented list into segments of about `target` entries and
+// uploads them; the segment array only grows.
+static cudaError_t set_segments(snap_layout *h, AllocCounter &ac, int32_t target, cudaStream_t stream) {
+    std::vector<int4> segs;
+    pack_segments(h->act_rp_host, target, h->graph_offsets, segs);
+    cudaError_t err = cudaSuccess;
+    if (segs.size() > h->act_seg_capacity || !h->d_act_seg) {
+        int4 *fresh = nullptr;
+        const size_t cap = segs.empty() ? 1 : segs.size();
+        err = dev_alloc(ac, (void **)&fresh, sizeof(int4) * cap, stream);
+        if (err != cudaSuccess) return err;
+        if (h->d_act_seg) {
+            cudaFreeAsync(h->d_act_seg, stream);
+            h->device_bytes -= (int64_t)(sizeof(int4) * h->act_seg_capacity);
+        }
+        h->d_act_seg = fresh;
+        h->act_seg_capacity = cap;
+        h->device_bytes += (int64_t)(sizeof(int4) * cap);
+    }
+    if (!segs.empty()) {
+        err = cudaMemcpyAsync(h->d_act_seg, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+        if (err != cudaSuccess) return err;
+    }
+    h->act_seg_len = target;
+    h->act_num_segs = (int64_t)segs.size();
+    // segment order multiplier: coprime with the segment count, near its golden section
+    int64_t m = (int64_t)(0.6180339887498949 * (double)h->act_num_segs) | 1;
+    while (h->act_num_segs > 1 && gcd64(m, h->act_num_segs) != 1) m += 2;
+    h->perm_mul = h->act_num_segs > 1 ? m % h->act_num_segs : 0;
+    if (h->act_num_segs > 1 && h->perm_mul == 0) h->perm_mul = 1;
+    return cudaSuccess;
+}
+
 // Builds the oriented bundle list from the validated device CSR and then
 // frees the CSR (the HOGWILD kernels and the objective need only the list).
 static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t stream) {
@@ -200,13 +359,12 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     const int64_t nnz = h->nnz;
     h->act_nnz = nnz / 2;   // symmetric and loop-free: each undirected edge once
     if (h->act_seg_len == 0) {
-        // Default segment size.  Concurrency degrades Hogwild quality when a
-        // large share of the graph is in flight at once, so graphs that fill
-        // the device's lanes (about 512 per SM) fewer than four times over at
-        // 32 entries per segment get 128-entry segments; larger graphs get 32
-        // (shorter tails, same quality: their in-flight share is small).
-        const int64_t lanes = (int64_t)h->sms * 512;
-        h->act_seg_len = h->act_nnz >= 4 * 32 * lanes ? 32 : 128;
+        // Default segment size: 4 entries.  A lane applies a segment's steps
+        // of one source back to back; long bursts of one source's steps move
+        // the layout away from Algorithm 1's shuffled order (R-MAT 2^17,
+        // sequential, eta0 = 1: +0.8% energy at 4 entries, +5% at 32, +10% at
+        // 128).  Concurrency is bounded separately (max_inflight).
+        h->act_seg_len = 4;
     }
     int32_t *flags = nullptr, *pos = nullptr;
     void *temp = nullptr;
@@ -215,7 +373,7 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     const char *what = "";
     auto alloc = [&](void **p, size_t bytes, bool keep, const char *nm) {
         if (err != cudaSuccess) return;
-        err = dev_alloc(ac, p, bytes);
+        err = dev_alloc(ac, p, bytes, stream);
         if (err != cudaSuccess) {
             what = nm;
         } else if (keep) {
@@ -249,28 +407,16 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
                              cudaMemcpyDeviceToHost, stream), "read oriented row offsets");
         step(cudaStreamSynchronize(stream), "orientation");
     }
-    cudaFree(flags);
-    cudaFree(pos);
-    cudaFree(temp);
+    if (flags) cudaFreeAsync(flags, stream);
+    if (pos) cudaFreeAsync(pos, stream);
+    if (temp) cudaFreeAsync(temp, stream);
     if (err != cudaSuccess) return cuda_fail(err, what);
     if (act_rp[(size_t)n] != h->act_nnz)
         return fail(SNAP_ERR_CUDA, "orientation produced %lld entries, expected %lld", (long long)act_rp[(size_t)n],
                     (long long)h->act_nnz);
-    std::vector<int4> segs;
-    pack_segments(act_rp, h->act_seg_len, segs);
-    h->act_num_segs = (int64_t)segs.size();
-    alloc((void **)&h->d_act_seg, sizeof(int4) * (segs.empty() ? 1 : segs.size()), true, "oriented segments");
-    if (err == cudaSuccess && !segs.empty()) {
-        step(cudaMemcpyAsync(h->d_act_seg, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, stream),
-             "copy oriented segments");
-        step(cudaStreamSynchronize(stream), "copy oriented segments");
-    }
-    if (err != cudaSuccess) return cuda_fail(err, what);
-    // segment order multiplier: coprime with the segment count, near its golden section
-    int64_t m = (int64_t)(0.6180339887498949 * (double)h->act_num_segs) | 1;
-    while (h->act_num_segs > 1 && gcd64(m, h->act_num_segs) != 1) m += 2;
-    h->perm_mul = h->act_num_segs > 1 ? m % h->act_num_segs : 0;
-    if (h->act_num_segs > 1 && h->perm_mul == 0) h->perm_mul = 1;
+    h->act_rp_host = std::move(act_rp);
+    err = set_segments(h, ac, h->act_seg_len, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "oriented segments");
     h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
                                  sizeof(int32_t) * (size_t)(h->num_segs * h->seg_len + 4) +
                                  sizeof(int32_t) * (size_t)(h->num_segs > 0 ? h->num_segs : 1));
@@ -290,6 +436,8 @@ void snap_options_default(snap_options *o) {
     o->sync_cap = 0.0f;
     o->segment_edges = 0;
     o->block_threads = 0;
+    o->flags = 0;
+    o->max_inflight = 0.0f;
 }
 
 const char *snap_last_error(void) { return g_last_error.c_str(); }
@@ -325,17 +473,29 @@ static snap_status check_options(const snap_options &o) {
     if (o.segment_edges != 0 && (o.segment_edges < 4 || o.segment_edges > 4096 || o.segment_edges % 4 != 0))
         return fail(SNAP_ERR_INVALID_ARG, "segment_edges = %d must be 0 or a multiple of 4 in [4, 4096]",
                     o.segment_edges);
+    if (o.flags & ~SNAP_FLAG_CUDA_GRAPH) return fail(SNAP_ERR_INVALID_ARG, "unknown flags 0x%x", o.flags);
+    if (!(o.max_inflight >= 0.0f) || !(o.max_inflight <= 1.0f))
+        return fail(SNAP_ERR_INVALID_ARG, "max_inflight must be in [0, 1]");
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 256 || o.block_threads % 32 != 0))
         return fail(SNAP_ERR_INVALID_ARG, "block_threads = %d must be 0 or a multiple of 32 in [32, 256]",
                     o.block_threads);
     return SNAP_OK;
 }
 
-snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *degrees, int32_t n,
-                               const snap_options *opts, void *cuda_stream, snap_layout_t *out) {
+static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *degrees, int32_t n,
+                               const int32_t *graph_offsets, int32_t num_graphs, const snap_options *opts,
+                               void *cuda_stream, snap_layout_t *out) {
     if (!out) return fail(SNAP_ERR_INVALID_ARG, "out is NULL");
     snap_status st = check_csr_host(row_ptr, col_idx, degrees, n);
     if (st != SNAP_OK) return st;
+    if (num_graphs < 1) return fail(SNAP_ERR_INVALID_ARG, "num_graphs = %d must be >= 1", num_graphs);
+    if (graph_offsets) {
+        if (graph_offsets[0] != 0 || graph_offsets[num_graphs] != n)
+            return fail(SNAP_ERR_INVALID_ARG, "graph_offsets must start at 0 and end at n");
+        for (int32_t g = 0; g < num_graphs; ++g)
+            if (graph_offsets[g + 1] <= graph_offsets[g])
+                return fail(SNAP_ERR_INVALID_ARG, "graph %d is empty or graph_offsets decreases", g);
+    }
     snap_options o;
     snap_options_default(&o);
     if (opts) o = *opts;
@@ -345,9 +505,18 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     snap_layout *h = new (std::nothrow) snap_layout();
     if (!h) return fail(SNAP_ERR_OUT_OF_MEMORY, "host allocation of the handle failed");
+    h->alloc_stream = stream;
+    if (cudaEventCreateWithFlags(&h->last_use, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(SNAP_ERR_CUDA, "event creation failed");
+    }
+    cudaEventRecord(h->last_use, stream);
     h->n = n;
     h->nnz = row_ptr[n];
     h->opts = o;
+    h->num_graphs = graph_offsets ? num_graphs : 1;
+    if (graph_offsets && num_graphs > 1) h->graph_offsets.assign(graph_offsets, graph_offsets + num_graphs + 1);
     // CSR segments: the synchronous kernel's unit of work (and the
     // validation pass); the HOGWILD modes use segments of oriented entries.
     h->seg_len = (o.mode == SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 32;
@@ -362,7 +531,7 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     const size_t disp_bytes = o.mode == SNAP_MODE_SYNC ? sizeof(long long) * 2 * (size_t)n : 0;
 #define SNAP_ALLOC(ptr, bytes)                                                        \
     do {                                                                              \
-        err = dev_alloc(ac, (void **)&(ptr), (bytes));                                \
+        err = dev_alloc(ac, (void **)&(ptr), (bytes), stream);                        \
         if (err != cudaSuccess) {                                                     \
             h->release();                                                             \
             delete h;                                                                 \
@@ -378,6 +547,10 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     SNAP_ALLOC(h->d_status, sizeof(uint32_t) * 4);
     SNAP_ALLOC(h->d_partial, sizeof(double) * 2 * kObjGrid);
     if (disp_bytes) SNAP_ALLOC(h->d_disp, disp_bytes);
+    if (h->num_graphs > 1) {
+        SNAP_ALLOC(h->d_node_graph, sizeof(int32_t) * (size_t)n);
+        SNAP_ALLOC(h->d_graphs, sizeof(GraphInfo) * (size_t)h->num_graphs);
+    }
 #undef SNAP_ALLOC
 
 #define SNAP_CUDA(call, what)                                                         \
@@ -391,7 +564,8 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
             return cuda_fail(err, what);                                              \
         }                                                                             \
     } while (0)
-    SNAP_CUDA(cudaMallocHost((void **)&h->h_status, sizeof(uint32_t) * 4), "pinned status word");
+    h->h_status = g_status_slots.take();
+    SNAP_CUDA(h->h_status ? cudaSuccess : cudaErrorMemoryAllocation, "pinned status word");
     SNAP_CUDA(cudaEventCreateWithFlags(&h->status_event, cudaEventDisableTiming), "status event");
     std::vector<int32_t> deg((size_t)n);
     for (int32_t i = 0; i < n; ++i) deg[(size_t)i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
@@ -405,11 +579,27 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     SNAP_CUDA(cudaMemcpyAsync(h->d_deg, deg.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, stream),
               "copy degrees");
     SNAP_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t) * 4, stream), "clear status");
+    std::vector<int32_t> node_graph;
+    if (h->num_graphs > 1) {
+        node_graph.resize((size_t)n);
+        h->h_graphs.assign((size_t)h->num_graphs, GraphInfo{});
+        for (int32_t g = 0; g < h->num_graphs; ++g) {
+            for (int32_t v = graph_offsets[g]; v < graph_offsets[g + 1]; ++v) node_graph[(size_t)v] = g;
+            GraphInfo &gi = h->h_graphs[(size_t)g];
+            gi.node_base = graph_offsets[g];
+            gi.n = graph_offsets[g + 1] - graph_offsets[g];
+            gi.edge_base = row_ptr[graph_offsets[g]];
+        }
+        SNAP_CUDA(cudaMemcpyAsync(h->d_node_graph, node_graph.data(), sizeof(int32_t) * (size_t)n,
+                                  cudaMemcpyHostToDevice, stream), "copy vertex graphs");
+        SNAP_CUDA(cudaMemcpyAsync(h->d_graphs, h->h_graphs.data(), sizeof(GraphInfo) * h->h_graphs.size(),
+                                  cudaMemcpyHostToDevice, stream), "copy graph table");
+    }
     if (h->d_disp) SNAP_CUDA(cudaMemsetAsync(h->d_disp, 0, disp_bytes, stream), "clear displacement");
     SNAP_CUDA(launch_segment_rows(h->d_row_ptr, n, h->nnz, h->seg_len, h->d_seg_row, h->num_segs, stream),
               "segment table kernel");
     SNAP_CUDA(launch_validate_csr(h->d_row_ptr, h->d_col, h->d_seg_row, n, h->nnz, h->seg_len, h->d_status + 1,
-                                  stream), "validation kernel");
+                                  stream, h->d_node_graph), "validation kernel");
     SNAP_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, stream),
               "read validation word");
     SNAP_CUDA(cudaStreamSynchronize(stream), "create");
@@ -421,6 +611,7 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
         if (vflags & kBadColumn) return fail(SNAP_ERR_INVALID_ARG, "col_idx holds a column outside [0, n)");
         if (vflags & kSelfLoop) return fail(SNAP_ERR_INVALID_ARG, "col_idx holds a self-loop (j == i)");
         if (vflags & kUnsorted) return fail(SNAP_ERR_INVALID_ARG, "a row of col_idx is not strictly ascending");
+        if (vflags & kCrossGraph) return fail(SNAP_ERR_INVALID_ARG, "an edge joins two graphs of the batch");
         return fail(SNAP_ERR_INVALID_ARG, "the CSR is not symmetric: some (i, j) has no (j, i)");
     }
     h->h_status[0] = 0;
@@ -460,6 +651,18 @@ snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, c
     return SNAP_OK;
 }
 
+snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *degrees, int32_t n,
+                               const snap_options *opts, void *cuda_stream, snap_layout_t *out) {
+    return create_impl(row_ptr, col_idx, degrees, n, nullptr, 1, opts, cuda_stream, out);
+}
+
+snap_status snap_layout_create_batch(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
+                                     const int32_t *graph_offsets, int32_t num_graphs, const snap_options *opts,
+                                     void *cuda_stream, snap_layout_t *out) {
+    if (!graph_offsets) return fail(SNAP_ERR_INVALID_ARG, "graph_offsets is NULL");
+    return create_impl(row_ptr, col_idx, nullptr, n, graph_offsets, num_graphs, opts, cuda_stream, out);
+}
+
 static snap_status poll_status(snap_layout *h) {
     if (h->status_pending && cudaEventQuery(h->status_event) == cudaSuccess) {
         h->status_pending = false;
@@ -485,23 +688,25 @@ static snap_status check_schedule(const snap_schedule *s) {
     return SNAP_OK;
 }
 
-snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
-                               int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
-                               void *cuda_stream) {
-    if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
-    if (!positions) return fail(SNAP_ERR_INVALID_ARG, "positions is NULL");
-    if (((uintptr_t)positions & 7u) != 0) return fail(SNAP_ERR_INVALID_ARG, "positions must be 8-byte aligned");
-    if (epochs < 0 || epoch_begin < 0) return fail(SNAP_ERR_INVALID_ARG, "epoch_begin and epochs must be >= 0");
-    if (neg_samples < 0 || neg_samples > 64) return fail(SNAP_ERR_INVALID_ARG, "neg_samples = %d out of [0, 64]",
-                                                         neg_samples);
-    snap_status st = check_schedule(schedule);
-    if (st != SNAP_OK) return st;
-    st = poll_status(h);
-    if (st != SNAP_OK) return st;
-    if (h->nnz == 0 || epochs == 0) return SNAP_OK;
+// Grid of a HOGWILD epoch: enough blocks for every segment, at most the
+// resident maximum, and at most max_inflight * entries lanes (one entry in
+// flight per lane), so small graphs are not updated by too many lanes at
+// once (each lane grid-strides over several segments instead).
+static int inflight_grid(const snap_layout *h, int gmax) {
+    const int64_t want = (h->act_num_segs + h->block - 1) / h->block;
+    int64_t grid = want < gmax ? want : gmax;
+    const double frac = h->opts.max_inflight > 0.0f ? (double)h->opts.max_inflight : 0.01;
+    const int64_t lanes_cap = (int64_t)(frac * (double)h->act_nnz);
+    const int64_t grid_cap = (lanes_cap + h->block - 1) / h->block;
+    if (grid_cap < grid) grid = grid_cap;
+    return grid > 0 ? (int)grid : 1;
+}
 
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
-    float2 *pos = reinterpret_cast<float2 *>(positions);
+// Enqueues the launches of epochs [epoch_begin, epoch_begin + epochs) on `stream`.
+static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_begin, int32_t epochs,
+                                  int32_t neg_samples, const snap_schedule &sched, uint64_t seed,
+                                  cudaStream_t stream) {
+    const snap_schedule *schedule = &sched;
     cudaError_t err = cudaSuccess;
     for (int32_t ep = 0; ep < epochs; ++ep) {
         const int32_t t = epoch_begin + ep;
@@ -526,6 +731,8 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
                     a.epoch = (uint32_t)t;
                     a.seed = seed;
                     a.status = h->d_status;
+                    a.node_graph = h->d_node_graph;
+                    a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
                     const int64_t segs = (ee + h->seg_len - 1) / h->seg_len - eb / h->seg_len;
                     const int64_t want = (segs + h->block - 1) / h->block;
                     const int grid = (int)(want < h->grid_sync ? want : h->grid_sync);
@@ -533,7 +740,8 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
                 }
                 if (err == cudaSuccess)
                     err = launch_sync_apply(pos, h->d_disp, h->n, (float)eta, (float)limit, h->d_status,
-                                            h->grid_apply, 256, stream);
+                                            h->grid_apply, 256, stream, h->d_node_graph,
+                                            h->num_graphs > 1 ? h->d_graphs : nullptr, t, h->opts.sync_cap);
             }
         } else {
             OrientedArgs a;
@@ -550,16 +758,108 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
             a.seed = seed;
             a.eta = (float)eta;
             a.status = h->d_status;
+            a.node_graph = h->d_node_graph;
+            a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
             const int g = neg_samples < 4 ? neg_samples : 4;
-            if (h->grid_oriented[red][g] == 0)
-                h->grid_oriented[red][g] = h->sms * oriented_blocks_per_sm(red, neg_samples, h->block);
             const int gmax = h->grid_oriented[red][g];
-            const int64_t want = (h->act_num_segs + h->block - 1) / h->block;
             if (h->act_num_segs == 0) continue;
-            const int grid = (int)(want < gmax ? want : gmax);
+            const int grid = inflight_grid(h, gmax);
+            {
+                // lanes beyond the segment count are idle
+                const double lanes = (double)grid * h->block;
+                const double segs = (double)h->act_num_segs;
+                a.inflight_share = (float)((lanes < segs ? lanes : segs) / segs);
+            }
             err = launch_oriented_epoch(a, red, grid > 0 ? grid : 1, h->block, stream);
         }
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
+                               int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                               void *cuda_stream) {
+    if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
+    if (!positions) return fail(SNAP_ERR_INVALID_ARG, "positions is NULL");
+    if (((uintptr_t)positions & 7u) != 0) return fail(SNAP_ERR_INVALID_ARG, "positions must be 8-byte aligned");
+    if (epochs < 0 || epoch_begin < 0) return fail(SNAP_ERR_INVALID_ARG, "epoch_begin and epochs must be >= 0");
+    if (neg_samples < 0 || neg_samples > 64) return fail(SNAP_ERR_INVALID_ARG, "neg_samples = %d out of [0, 64]",
+                                                         neg_samples);
+    snap_status st = check_schedule(schedule);
+    if (st != SNAP_OK) return st;
+    st = poll_status(h);
+    if (st != SNAP_OK) return st;
+    if (h->nnz == 0 || epochs == 0) return SNAP_OK;
+
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    float2 *pos = reinterpret_cast<float2 *>(positions);
+    cudaError_t err = cudaSuccess;
+    if (h->num_graphs > 1) {
+        // every graph of the batch runs the call's schedule and seed from epoch 0
+        const snap_schedule &sc = *schedule;
+        if (!h->graphs_set || h->graphs_seed != seed || memcmp(&h->graphs_sched, &sc, sizeof(sc)) != 0) {
+            for (GraphInfo &gi : h->h_graphs) {
+                gi.seed = seed;
+                gi.start_tick = 0;
+                gi.total_epochs = sc.kind == 1 ? INT32_MAX : sc.total_epochs;
+                gi.eta0 = sc.eta0;
+                gi.eta_min = sc.eta_min;
+                gi.kind = sc.kind;
+            }
+            err = cudaMemcpyAsync(h->d_graphs, h->h_graphs.data(), sizeof(GraphInfo) * h->h_graphs.size(),
+                                  cudaMemcpyHostToDevice, stream);
+            if (err != cudaSuccess) return cuda_fail(err, "copy graph table");
+            h->graphs_set = true;
+            h->graphs_sched = sc;
+            h->graphs_seed = seed;
+        }
+    }
+    if (h->opts.mode != SNAP_MODE_SYNC) {
+        // occupancy query outside any capture
+        const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
+        const int g = neg_samples < 4 ? neg_samples : 4;
+        if (h->grid_oriented[red][g] == 0)
+            h->grid_oriented[red][g] =
+                h->sms * oriented_blocks_per_sm(red, neg_samples, h->block, h->num_graphs > 1);
+    }
+    if ((h->opts.flags & SNAP_FLAG_CUDA_GRAPH) && epochs > 1) {
+        cudaGraphExec_t exec = nullptr;
+        for (const CapturedEpochs &c : h->captured)
+            if (c.pos == positions && c.epoch_begin == epoch_begin && c.epochs == epochs && c.k == neg_samples &&
+                c.seed == seed && memcmp(&c.sched, schedule, sizeof(snap_schedule)) == 0)
+                exec = c.exec;
+        if (!exec) {
+            if (!h->capture_stream) {
+                err = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+                if (err != cudaSuccess) return cuda_fail(err, "capture stream");
+            }
+            // the capture stream must see the work already queued on the caller's stream
+            cudaGraph_t graph = nullptr;
+            err = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                const cudaError_t e2 = enqueue_epochs(h, pos, epoch_begin, epochs, neg_samples, *schedule, seed,
+                                                      h->capture_stream);
+                err = cudaStreamEndCapture(h->capture_stream, &graph);
+                if (e2 != cudaSuccess) err = e2;
+            }
+            if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (err != cudaSuccess) {
+                cudaGetLastError();
+                return cuda_fail(err, "epoch graph capture");
+            }
+            if (h->captured.size() >= 4) {
+                cudaGraphExecDestroy(h->captured.front().exec);
+                h->captured.erase(h->captured.begin());
+            }
+            h->captured.push_back(CapturedEpochs{positions, epoch_begin, epochs, neg_samples, seed, *schedule, exec});
+        }
+        err = cudaGraphLaunch(exec, stream);
+        if (err != cudaSuccess) return cuda_fail(err, "epoch graph launch");
+    } else {
+        err = enqueue_epochs(h, pos, epoch_begin, epochs, neg_samples, *schedule, seed, stream);
         if (err != cudaSuccess) return cuda_fail(err, "epoch launch");
     }
     if (!h->status_pending) {
@@ -568,6 +868,7 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
         if (err != cudaSuccess) return cuda_fail(err, "status read-back");
         h->status_pending = true;
     }
+    h->mark_use(stream);
     return SNAP_OK;
 }
 
@@ -610,8 +911,13 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
             err = launch_objective_oriented(h->d_act_row_ptr, h->d_act_ent, h->d_act_seg, h->act_num_segs, pos,
                                             h->d_partial, kObjGrid, stream);
     }
+    if (h->num_graphs > 1 && !exact)
+        return fail(SNAP_ERR_NOT_SUPPORTED, "the sampled objective is not available for a batch (use exact = 1)");
     if (err == cudaSuccess && h->n > 1) {
-        if (exact)
+        if (h->num_graphs > 1)
+            err = launch_objective_pairs_batch(pos, h->d_deg, h->d_node_graph, h->d_graphs, h->n,
+                                               h->d_partial + kObjGrid, kObjGrid, stream);
+        else if (exact)
             err = launch_objective_pairs_exact(pos, h->d_deg, h->n, h->d_partial + kObjGrid, kObjGrid, stream);
         else
             err = launch_objective_pairs_sampled(pos, h->d_deg, h->n, pair_samples, seed, h->d_partial + kObjGrid,
@@ -623,11 +929,14 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
                               stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
     if (err != cudaSuccess) return cuda_fail(err, "objective");
+    h->mark_use(stream);
     double attr = 0.0, pairsum = 0.0;
     for (int b = 0; b < kObjGrid; ++b) attr += part[(size_t)b];
     for (int b = 0; b < kObjGrid; ++b) pairsum += part[(size_t)kObjGrid + b];
     double rep = 0.0;
-    if (h->n > 1) {
+    if (h->num_graphs > 1) {
+        rep = (double)neg_samples * 0.5 * pairsum;   // per-graph weights applied on the device
+    } else if (h->n > 1) {
         const double n = (double)h->n;
         // unordered-pair sum of (d_i + d_j) U^r
         const double unordered = exact ? 0.5 * pairsum : pairsum / (double)pair_samples * 0.5 * n * (n - 1.0);
@@ -640,6 +949,81 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
 }
 
 int64_t snap_layout_device_bytes(snap_layout_t h) { return h ? h->device_bytes : 0; }
+
+snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int32_t neg_samples, double max_inflight,
+                                 int32_t *chosen_segment, int32_t *chosen_block, double *chosen_ms,
+                                 void *cuda_stream) {
+    if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
+    if (h->opts.mode == SNAP_MODE_SYNC) return fail(SNAP_ERR_NOT_SUPPORTED, "autotuning applies to the HOGWILD modes");
+    if (!scratch_positions || ((uintptr_t)scratch_positions & 7u) != 0)
+        return fail(SNAP_ERR_INVALID_ARG, "scratch_positions must be a non-NULL 8-byte aligned device buffer");
+    if (neg_samples < 0 || neg_samples > 64) return fail(SNAP_ERR_INVALID_ARG, "neg_samples out of [0, 64]");
+    if (!(max_inflight > 0.0)) max_inflight = 1.0 / 64.0;
+    snap_status st = poll_status(h);
+    if (st != SNAP_OK) return st;
+    if (h->act_nnz == 0) return fail(SNAP_ERR_INVALID_ARG, "the graph has no edges");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const int32_t targets[] = {4, 8, 16, 32};
+    const int32_t blocks[] = {128, 256};
+    const snap_schedule sched{1, 1, 1.0, 1.0};   // constant step: timing only
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int32_t keep_target = h->act_seg_len, keep_block = h->block;
+    int32_t best_t = keep_target, best_b = keep_block;
+    double best_ms = 1e300;
+    AllocCounter ac;
+    cudaError_t err = cudaSuccess;
+    for (int32_t target : targets) {
+        // lanes in flight: one entry each; their share of the graph bounds concurrency
+        for (int32_t block : blocks) {
+            const int g = neg_samples < 4 ? neg_samples : 4;
+            const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
+            (void)max_inflight;
+            if ((err = set_segments(h, ac, target, stream)) != cudaSuccess) break;
+            h->block = block;
+            h->grid_oriented[red][g] = 0;
+            h->grid_oriented[red][g] = h->sms * oriented_blocks_per_sm(red, neg_samples, block, h->num_graphs > 1);
+            err = enqueue_epochs(h, reinterpret_cast<float2 *>(scratch_positions), 0, 1, neg_samples, sched, 1,
+                                 stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, stream);
+            if (err == cudaSuccess)
+                err = enqueue_epochs(h, reinterpret_cast<float2 *>(scratch_positions), 1, 2, neg_samples, sched, 1,
+                                     stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) break;
+            if (ms / 2.0 < best_ms) {
+                best_ms = ms / 2.0;
+                best_t = target;
+                best_b = block;
+            }
+        }
+        if (err != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err == cudaSuccess) {
+        err = set_segments(h, ac, best_t, stream);
+        h->block = best_b;
+        for (auto &row : h->grid_oriented)
+            for (int &v : row) v = 0;
+        for (const CapturedEpochs &c : h->captured) cudaGraphExecDestroy(c.exec);
+        h->captured.clear();
+    }
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(err, "autotune");
+    }
+    if (best_ms == 1e300) return fail(SNAP_ERR_INVALID_ARG, "no candidate satisfies max_inflight");
+    h->mark_use(stream);
+    if (chosen_segment) *chosen_segment = best_t;
+    if (chosen_block) *chosen_block = best_b;
+    if (chosen_ms) *chosen_ms = best_ms;
+    return snap_layout_check(h, cuda_stream);
+}
 
 void snap_layout_destroy(snap_layout_t h) {
     if (!h) return;
@@ -662,7 +1046,7 @@ snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int3
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     float *d_pos = nullptr;
     const size_t bytes = sizeof(float) * 2 * (size_t)n;
-    cudaError_t err = dev_alloc(g_alloc, (void **)&d_pos, bytes);
+    cudaError_t err = dev_alloc(g_alloc, (void **)&d_pos, bytes, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         snap_layout_destroy(h);
@@ -670,7 +1054,7 @@ snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int3
     }
     err = cudaMemcpyAsync(d_pos, positions_host, bytes, cudaMemcpyHostToDevice, stream);
     if (err != cudaSuccess) {
-        cudaFree(d_pos);
+        cudaFreeAsync(d_pos, stream);
         snap_layout_destroy(h);
         return cuda_fail(err, "copy positions to the device");
     }
@@ -681,9 +1065,171 @@ snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int3
         if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
         if (err != cudaSuccess) st = cuda_fail(err, "copy positions to the host");
     }
-    cudaFree(d_pos);
+    cudaFreeAsync(d_pos, stream);
     snap_layout_destroy(h);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Multi-handle epochs (continuous batching)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct snap_multi {
+    int32_t capacity = 0;
+    JobDesc *d_jobs = nullptr;
+    JobDesc *h_jobs = nullptr;      // pinned staging of the job table
+    uint32_t *d_status = nullptr;
+    uint32_t *h_status = nullptr;   // pinned
+    cudaEvent_t copied = nullptr;
+    bool copy_pending = false;
+    int sms = 1;
+    int grid[2][5] = {{0}};
+    uint64_t calls = 0;
+
+    void release() {
+        cudaFree(d_jobs);
+        cudaFree(d_status);
+        if (h_jobs) cudaFreeHost(h_jobs);
+        if (h_status) cudaFreeHost(h_status);
+        if (copied) cudaEventDestroy(copied);
+        d_jobs = nullptr;
+        d_status = nullptr;
+        h_jobs = nullptr;
+        h_status = nullptr;
+        copied = nullptr;
+    }
+};
+
+extern "C" {
+
+snap_status snap_multi_create(int32_t max_jobs, snap_multi_t *out) {
+    if (!out) return fail(SNAP_ERR_INVALID_ARG, "out is NULL");
+    if (max_jobs < 1 || max_jobs > (1 << 20)) return fail(SNAP_ERR_INVALID_ARG, "max_jobs out of [1, 2^20]");
+    snap_multi *m = new (std::nothrow) snap_multi();
+    if (!m) return fail(SNAP_ERR_OUT_OF_MEMORY, "host allocation failed");
+    m->capacity = max_jobs;
+    cudaError_t err = cudaMalloc((void **)&m->d_jobs, sizeof(JobDesc) * (size_t)max_jobs);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&m->d_status, sizeof(uint32_t) * 4);
+    if (err == cudaSuccess) err = cudaMallocHost((void **)&m->h_jobs, sizeof(JobDesc) * (size_t)max_jobs);
+    if (err == cudaSuccess) err = cudaMallocHost((void **)&m->h_status, sizeof(uint32_t) * 4);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&m->copied, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaMemset(m->d_status, 0, sizeof(uint32_t) * 4);
+    int dev = 0;
+    if (err == cudaSuccess) err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) {
+        m->release();
+        delete m;
+        cudaGetLastError();
+        return cuda_fail(err, "snap_multi_create");
+    }
+    *out = m;
+    return SNAP_OK;
+}
+
+snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float *const *positions,
+                             const int32_t *epochs, const snap_schedule *schedules, const uint64_t *seeds,
+                             int32_t count, int32_t neg_samples, void *cuda_stream) {
+    if (!m || !handles || !positions || !epochs || !schedules || !seeds)
+        return fail(SNAP_ERR_INVALID_ARG, "NULL argument");
+    if (count < 0 || count > m->capacity) return fail(SNAP_ERR_INVALID_ARG, "count = %d out of [0, %d]", count,
+                                                      m->capacity);
+    if (neg_samples < 0 || neg_samples > 64) return fail(SNAP_ERR_INVALID_ARG, "neg_samples out of [0, 64]");
+    int red = -1;
+    for (int32_t q = 0; q < count; ++q) {
+        const snap_layout *h = handles[q];
+        if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle %d is NULL", q);
+        if (h->opts.mode == SNAP_MODE_SYNC || h->num_graphs > 1)
+            return fail(SNAP_ERR_NOT_SUPPORTED, "handle %d: multi-handle epochs take single-graph HOGWILD handles", q);
+        const int r = h->opts.mode == SNAP_MODE_HOGWILD_RED;
+        if (red >= 0 && r != red) return fail(SNAP_ERR_INVALID_ARG, "handles mix HOGWILD and HOGWILD_RED");
+        red = r;
+        if (!positions[q] || ((uintptr_t)positions[q] & 7u) != 0)
+            return fail(SNAP_ERR_INVALID_ARG, "positions[%d] is NULL or misaligned", q);
+        if (epochs[q] < 0) return fail(SNAP_ERR_INVALID_ARG, "epochs[%d] < 0", q);
+        const snap_status st = check_schedule(&schedules[q]);
+        if (st != SNAP_OK) return st;
+    }
+    if (m->copy_pending) {
+        // the staging buffer may be rewritten once the previous table reached the device
+        const cudaError_t e = cudaEventSynchronize(m->copied);
+        if (e != cudaSuccess) return cuda_fail(e, "multi staging");
+        m->copy_pending = false;
+    }
+    int64_t total = 0;
+    int32_t used = 0;
+    uint64_t mixkey = 0x243F6A8885A308D3ull ^ ++m->calls;
+    for (int32_t q = 0; q < count; ++q) {
+        const snap_layout *h = handles[q];
+        if (h->act_num_segs == 0) continue;
+        JobDesc &jd = m->h_jobs[used++];
+        jd.row_ptr = h->d_act_row_ptr;
+        jd.ent = h->d_act_ent;
+        jd.seg = h->d_act_seg;
+        jd.pos = reinterpret_cast<float2 *>(positions[q]);
+        jd.num_segs = h->act_num_segs;
+        jd.seg_prefix = total;
+        jd.seed = seeds[q];
+        jd.n = h->n;
+        jd.epoch = (uint32_t)epochs[q];
+        jd.eta = (float)step_size(schedules[q], epochs[q]);
+        total += h->act_num_segs;
+        mixkey = mix64(mixkey ^ seeds[q] ^ ((uint64_t)epochs[q] << 32));
+    }
+    if (used == 0 || red < 0) return SNAP_OK;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    cudaError_t err = cudaMemcpyAsync(m->d_jobs, m->h_jobs, sizeof(JobDesc) * (size_t)used, cudaMemcpyHostToDevice,
+                                      stream);
+    if (err == cudaSuccess) err = cudaEventRecord(m->copied, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "copy job table");
+    m->copy_pending = true;
+    MultiArgs a;
+    a.jobs = m->d_jobs;
+    a.num_jobs = used;
+    a.k = neg_samples;
+    a.total_segs = total;
+    int64_t mul = (int64_t)(0.6180339887498949 * (double)total) | 1;
+    while (total > 1 && gcd64(mul, total) != 1) mul += 2;
+    a.perm_mul = total > 1 ? mul % total : 0;
+    if (total > 1 && a.perm_mul == 0) a.perm_mul = 1;
+    a.perm_add = (int64_t)(mixkey % (uint64_t)total);
+    a.status = m->d_status;
+    const int g = neg_samples < 4 ? neg_samples : 4;
+    if (m->grid[red][g] == 0) m->grid[red][g] = m->sms * multi_blocks_per_sm(red, neg_samples, 256);
+    // at most 1% of the jobs' entries in flight (as inflight_grid does for one handle)
+    int64_t entries = 0;
+    for (int32_t q = 0; q < count; ++q) entries += handles[q]->act_nnz;
+    const int64_t want = (total + 255) / 256;
+    int64_t gcap = ((int64_t)(0.01 * (double)entries) + 255) / 256;
+    int64_t gl = want < m->grid[red][g] ? want : m->grid[red][g];
+    if (gcap < gl) gl = gcap;
+    const int grid = (int)(gl > 0 ? gl : 1);
+    a.inflight_share = (float)(((double)grid * 256.0 < (double)total ? (double)grid * 256.0 : (double)total) /
+                               (double)total);
+    err = launch_multi_epoch(a, red, grid > 0 ? grid : 1, 256, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "multi-handle epoch launch");
+    for (int32_t q = 0; q < count; ++q) handles[q]->mark_use(stream);
+    return SNAP_OK;
+}
+
+snap_status snap_multi_check(snap_multi_t m, void *cuda_stream) {
+    if (!m) return fail(SNAP_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t err = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (err == cudaSuccess) err = cudaMemcpy(m->h_status, m->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return cuda_fail(err, "multi check");
+    if (m->h_status[0]) {
+        cudaMemset(m->d_status, 0, sizeof(uint32_t));
+        return fail(SNAP_ERR_NUMERIC, "a multi-handle epoch produced a non-finite position");
+    }
+    return SNAP_OK;
+}
+
+void snap_multi_destroy(snap_multi_t m) {
+    if (!m) return;
+    if (m->copy_pending) cudaEventSynchronize(m->copied);
+    m->release();
+    delete m;
 }
 
 }  // extern "C"

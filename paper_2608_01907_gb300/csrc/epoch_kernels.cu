@@ -48,6 +48,57 @@ __device__ __forceinline__ void apply_partner(float2 *pos, int32_t idx, float2 n
 // partner of every neighbour's bundle.
 // ---------------------------------------------------------------------------
 
+// Per-lane view of the graph the current segment belongs to.
+struct GraphCtx {
+    int32_t base;        // first vertex of the graph
+    uint32_t nm1;        // n_g - 1
+    int64_t edge_base;   // first directed edge of the graph (random-word index origin)
+    uint32_t epoch;      // the graph's epoch
+    float eta;
+    uint2 key;           // Philox key (the graph's seed)
+    bool active;
+};
+
+__device__ __forceinline__ int32_t negative_in(const GraphCtx &c, uint32_t w, int32_t src) {
+    return c.base + negative_of(w, src - c.base, c.nm1);
+}
+
+__device__ __forceinline__ uint4 words_in(const GraphCtx &c, int64_t e, uint32_t g) {
+    return edge_words(e - c.edge_base, c.epoch, g, c.key);
+}
+
+// Step size of epoch t under a schedule (the same expression as the host's).
+__device__ __forceinline__ float schedule_eta(const GraphInfo &gi, int32_t t) {
+    if (gi.kind == 1) return (float)gi.eta0;
+    double eta = gi.eta0 * (1.0 - (double)t / (double)gi.total_epochs);
+    return (float)(eta > gi.eta_min ? eta : gi.eta_min);
+}
+
+template <bool MULTI>
+__device__ __forceinline__ GraphCtx graph_ctx(const OrientedArgs &a, int32_t row) {
+    GraphCtx c;
+    if (MULTI) {
+        const GraphInfo gi = a.graphs[__ldg(a.node_graph + row)];
+        const int32_t t = (int32_t)a.epoch - gi.start_tick;
+        c.base = gi.node_base;
+        c.nm1 = (uint32_t)(gi.n - 1);
+        c.edge_base = gi.edge_base;
+        c.epoch = (uint32_t)t;
+        c.key = make_uint2((uint32_t)gi.seed, (uint32_t)(gi.seed >> 32));
+        c.active = t >= 0 && t < gi.total_epochs;
+        c.eta = c.active ? schedule_eta(gi, t) : 0.0f;
+    } else {
+        c.base = 0;
+        c.nm1 = (uint32_t)(a.n - 1);
+        c.edge_base = 0;
+        c.epoch = a.epoch;
+        c.eta = a.eta;
+        c.key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        c.active = true;
+    }
+    return c;
+}
+
 // Negatives of one group (up to 4, already gathered into v[]) for source
 // `src` held in ysrc; the vertex `other` is register-resident in yoth.
 // s[] and v[] are updated in place (v[m] = the value after its update).
@@ -80,38 +131,38 @@ __device__ __forceinline__ void negative_group(float2 *pos, float eta, const int
 // Groups 1, 2, ... of negatives (k > 4): gathered after the earlier stores
 // of this lane, so memory already holds this lane's updates.
 template <bool RED>
-__device__ __forceinline__ void later_negatives(const OrientedArgs &a, int64_t ekey, int32_t src, float2 &ysrc,
-                                                int32_t other, float2 &yoth, uint2 key, uint32_t nm1) {
+__device__ __forceinline__ void later_negatives(const OrientedArgs &a, const GraphCtx &c, int64_t ekey, int32_t src,
+                                                float2 &ysrc, int32_t other, float2 &yoth) {
     for (int g = 1; g * 4 < a.k; ++g) {
         const int nm = a.k - 4 * g < 4 ? a.k - 4 * g : 4;
-        const uint4 w = edge_words(ekey, a.epoch, (uint32_t)g, key);
-        int32_t s[4] = {negative_of(w.x, src, nm1), negative_of(w.y, src, nm1), negative_of(w.z, src, nm1),
-                        negative_of(w.w, src, nm1)};
+        const uint4 w = words_in(c, ekey, (uint32_t)g);
+        int32_t s[4] = {negative_in(c, w.x, src), negative_in(c, w.y, src), negative_in(c, w.z, src),
+                        negative_in(c, w.w, src)};
         float2 v[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             if (m < nm) v[m] = load_pos(a.pos + s[m]);
-        negative_group<RED>(a.pos, a.eta, s, v, nm, ysrc, other, yoth);
+        negative_group<RED>(a.pos, c.eta, s, v, nm, ysrc, other, yoth);
     }
 }
 
 template <bool RED, int G>
-__device__ __forceinline__ void oriented_entry(const OrientedArgs &a, int32_t i, int32_t j, int32_t e1, int32_t e2,
-                                               float2 &yi, uint2 key, uint32_t nm1) {
-    const float eta = a.eta;
+__device__ __forceinline__ void oriented_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, int32_t j,
+                                               int32_t e1, int32_t e2, float2 &yi) {
+    const float eta = c.eta;
     int32_t s1[4] = {0, 0, 0, 0}, s2[4] = {0, 0, 0, 0};
     float2 v1[4], v2[4];
     if (G > 0) {
-        const uint4 w1 = edge_words(e1, a.epoch, 0u, key);
-        const uint4 w2 = edge_words(e2, a.epoch, 0u, key);
-        s1[0] = negative_of(w1.x, i, nm1);
-        s1[1] = negative_of(w1.y, i, nm1);
-        s1[2] = negative_of(w1.z, i, nm1);
-        s1[3] = negative_of(w1.w, i, nm1);
-        s2[0] = negative_of(w2.x, j, nm1);
-        s2[1] = negative_of(w2.y, j, nm1);
-        s2[2] = negative_of(w2.z, j, nm1);
-        s2[3] = negative_of(w2.w, j, nm1);
+        const uint4 w1 = words_in(c, e1, 0u);
+        const uint4 w2 = words_in(c, e2, 0u);
+        s1[0] = negative_in(c, w1.x, i);
+        s1[1] = negative_in(c, w1.y, i);
+        s1[2] = negative_in(c, w1.z, i);
+        s1[3] = negative_in(c, w1.w, i);
+        s2[0] = negative_in(c, w2.x, j);
+        s2[1] = negative_in(c, w2.y, j);
+        s2[2] = negative_in(c, w2.z, j);
+        s2[3] = negative_in(c, w2.w, j);
     }
     const bool prefetch2 = a.k <= 4;   // group 0 of direction 2 can be gathered up front
     float2 yj = load_pos(a.pos + j);
@@ -132,7 +183,7 @@ __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, int32_t i,
         yj.x -= df.x;
         yj.y -= df.y;
         if (G > 0) negative_group<RED>(a.pos, eta, s1, v1, G, yi, j, yj);
-        if (a.k > 4) later_negatives<RED>(a, e1, i, yi, j, yj, key, nm1);
+        if (a.k > 4) later_negatives<RED>(a, c, e1, i, yi, j, yj);
     }
     // direction 2: (j, i), source j
     {
@@ -156,23 +207,32 @@ __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, int32_t i,
             }
             negative_group<RED>(a.pos, eta, s2, v2, G, yj, i, yi);
         }
-        if (a.k > 4) later_negatives<RED>(a, e2, j, yj, i, yi, key, nm1);
+        if (a.k > 4) later_negatives<RED>(a, c, e2, j, yj, i, yi);
     }
     apply_partner<RED>(a.pos, j, yj, make_float2(yj.x - yj0.x, yj.y - yj0.y));
 }
 
-// Source write-back at the end of a row run.  HOGWILD stores the lane's copy;
-// HOGWILD_RED adds the lane's displacement, divided by the number of pieces
-// a long row was cut into, so a split bundle takes one sequential pass's step.
+// Source write-back at the end of a row run.
+// HOGWILD writes the lane's copy with an atomic exchange: the same
+// last-writer-wins result as a store, but a source cut into many pieces (a
+// hub) is written thousands of times per epoch, and L2 serialises plain
+// stores to one address behind the loads of it far more than atomics.
+// HOGWILD_RED adds the lane's displacement divided by the expected number of
+// pieces of the same row in flight together (pieces x lanes / segments, at
+// least 1): pieces that run at different times add up, pieces that start
+// from the same position are averaged.
 template <bool RED>
 __device__ __forceinline__ void write_oriented_source(const OrientedArgs &a, int32_t row, float2 yi, float2 yi0,
                                                       int pieces, uint32_t &flags) {
     if (!finite2(yi)) flags |= kStatusNonFinite;
     if (RED) {
-        const float inv = pieces > 1 ? 1.0f / (float)pieces : 1.0f;
+        const float together = (float)pieces * a.inflight_share;
+        const float inv = together > 1.0f ? 1.0f / together : 1.0f;
         atomicAdd(a.pos + row, make_float2((yi.x - yi0.x) * inv, (yi.y - yi0.y) * inv));
     } else {
-        store_pos(a.pos + row, yi);
+        unsigned long long bits;
+        memcpy(&bits, &yi, 8);
+        atomicExch(reinterpret_cast<unsigned long long *>(a.pos + row), bits);
     }
 }
 
@@ -180,16 +240,80 @@ __device__ __forceinline__ void write_oriented_source(const OrientedArgs &a, int
 #define SNAP_ORIENTED_MIN_BLOCKS 1
 #endif
 
-template <bool RED, int G>
+// Segments never span two graphs of a batch, so the graph is looked up once
+// per segment.
+template <bool RED, int G, bool MULTI>
 __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_kernel(const OrientedArgs a) {
-    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const uint32_t nm1 = (uint32_t)(a.n - 1);
     uint32_t flags = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.num_segs; w += stride) {
         const int64_t ws = (int64_t)(((uint64_t)a.perm_mul * (uint64_t)w + (uint64_t)a.perm_add) %
                                      (uint64_t)a.num_segs);
         const int4 sg = __ldg(a.seg + ws);   // {begin, end, first row, pieces}
+        int64_t p = sg.x;
+        const int64_t p1 = sg.y;
+        int32_t row = sg.z;
+        const GraphCtx c = graph_ctx<MULTI>(a, row);
+        if (!c.active) continue;
+        int64_t row_end = __ldg(a.row_ptr + row + 1);
+        float2 yi = load_pos(a.pos + row);
+        float2 yi0 = yi;
+        for (; p < p1; ++p) {
+            if (p >= row_end) {
+                write_oriented_source<RED>(a, row, yi, yi0, 1, flags);
+                do {
+                    ++row;
+                    row_end = __ldg(a.row_ptr + row + 1);
+                } while (row_end <= p);
+                yi = load_pos(a.pos + row);
+                yi0 = yi;
+            }
+            const int4 en = load_entry(a.ent + p);   // {j, index of (i, j), index of (j, i), -}
+            oriented_entry<RED, G>(a, c, row, en.x, en.y, en.z, yi);
+        }
+        write_oriented_source<RED>(a, row, yi, yi0, sg.w, flags);
+    }
+    if (flags) atomicOr(a.status, flags);
+}
+
+// Multi-handle epoch (continuous batching): one launch runs one epoch of
+// several independent layouts.  The segments of all jobs form one index
+// space; lane w takes segment perm(w), finds its job by binary search over
+// the jobs' segment prefixes, and processes it exactly as the single-graph
+// kernel would with that job's arrays, epoch, step and seed.
+template <bool RED, int G>
+__global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) multi_epoch_kernel(const MultiArgs m) {
+    uint32_t flags = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < m.total_segs; w += stride) {
+        const int64_t ws = (int64_t)(((uint64_t)m.perm_mul * (uint64_t)w + (uint64_t)m.perm_add) %
+                                     (uint64_t)m.total_segs);
+        int32_t lo = 0, hi = m.num_jobs - 1;   // last job with seg_prefix <= ws
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) / 2;
+            if (__ldg(&m.jobs[mid].seg_prefix) <= ws)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const JobDesc &jd = m.jobs[lo];
+        OrientedArgs a;
+        a.row_ptr = jd.row_ptr;
+        a.ent = jd.ent;
+        a.seg = jd.seg;
+        a.pos = jd.pos;
+        a.num_segs = jd.num_segs;
+        a.n = jd.n;
+        a.k = m.k;
+        a.epoch = jd.epoch;
+        a.seed = jd.seed;
+        a.eta = jd.eta;
+        a.status = m.status;
+        a.node_graph = nullptr;
+        a.graphs = nullptr;
+        a.inflight_share = m.inflight_share;
+        const GraphCtx c = graph_ctx<false>(a, 0);
+        const int4 sg = __ldg(a.seg + (ws - jd.seg_prefix));
         int64_t p = sg.x;
         const int64_t p1 = sg.y;
         int32_t row = sg.z;
@@ -206,23 +330,47 @@ __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_
                 yi = load_pos(a.pos + row);
                 yi0 = yi;
             }
-            const int4 en = load_entry(a.ent + p);   // {j, index of (i, j), index of (j, i), -}
-            oriented_entry<RED, G>(a, row, en.x, en.y, en.z, yi, key, nm1);
+            const int4 en = load_entry(a.ent + p);
+            oriented_entry<RED, G>(a, c, row, en.x, en.y, en.z, yi);
         }
         write_oriented_source<RED>(a, row, yi, yi0, sg.w, flags);
     }
-    if (flags) atomicOr(a.status, flags);
+    if (flags) atomicOr(m.status, flags);
 }
 
 // Synchronous chunk: positions frozen (read-only in this launch), every force
 // quantised and summed into disp with integer atomics; the source's terms
 // are summed in registers (integer addition, so the total is the same as
-// adding them one by one) and flushed once per row run.
+// adding them one by one) and flushed once per row run.  In a batch the
+// graph (vertex range, random-word origin, epoch) is looked up per row.
+template <bool MULTI>
+__device__ __forceinline__ GraphCtx sync_ctx(const SyncArgs &a, int32_t row) {
+    GraphCtx c;
+    if (MULTI) {
+        const GraphInfo gi = a.graphs[__ldg(a.node_graph + row)];
+        const int32_t t = (int32_t)a.epoch - gi.start_tick;
+        c.base = gi.node_base;
+        c.nm1 = (uint32_t)(gi.n - 1);
+        c.edge_base = gi.edge_base;
+        c.epoch = (uint32_t)t;
+        c.key = make_uint2((uint32_t)gi.seed, (uint32_t)(gi.seed >> 32));
+        c.active = t >= 0 && t < gi.total_epochs;
+    } else {
+        c.base = 0;
+        c.nm1 = (uint32_t)(a.n - 1);
+        c.edge_base = 0;
+        c.epoch = a.epoch;
+        c.key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        c.active = true;
+    }
+    c.eta = 0.0f;
+    return c;
+}
+
+template <bool MULTI>
 __global__ void __launch_bounds__(256) sync_chunk_kernel(const SyncArgs a) {
     const int64_t seg_first = a.e_begin / a.seg_len;
     const int64_t seg_last = (a.e_end + a.seg_len - 1) / a.seg_len;   // exclusive
-    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const uint32_t nm1 = (uint32_t)(a.n - 1);
     uint32_t flags = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t seg = seg_first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; seg < seg_last;
@@ -235,6 +383,7 @@ __global__ void __launch_bounds__(256) sync_chunk_kernel(const SyncArgs a) {
             ++row;
             row_end = __ldg(a.row_ptr + row + 1);
         }
+        GraphCtx c = sync_ctx<MULTI>(a, row);
         float2 yi = __ldg(a.pos + row);
         long long accx = 0, accy = 0;
         for (int64_t eb = e0 & ~(int64_t)3; eb < e1; eb += 4) {
@@ -254,8 +403,10 @@ __global__ void __launch_bounds__(256) sync_chunk_kernel(const SyncArgs a) {
                             ++row;
                             row_end = __ldg(a.row_ptr + row + 1);
                         } while (row_end <= e);
+                        if (MULTI) c = sync_ctx<MULTI>(a, row);
                         yi = __ldg(a.pos + row);
                     }
+                    if (!c.active) continue;
                     const int32_t i = row;
                     const int32_t j = cols[q];
                     const float2 yj = __ldg(a.pos + j);
@@ -267,13 +418,13 @@ __global__ void __launch_bounds__(256) sync_chunk_kernel(const SyncArgs a) {
                     add_fixed(a.disp + 2 * (int64_t)j + 1, -fy);
                     for (int g = 0; g * 4 < a.k; ++g) {
                         const int nm = a.k - 4 * g < 4 ? a.k - 4 * g : 4;
-                        const uint4 w = edge_words(e, a.epoch, (uint32_t)g, key);
+                        const uint4 w = words_in(c, e, (uint32_t)g);
                         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
                         int32_t s[4];
                         float2 ys[4];
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
-                            s[m] = negative_of(ws[m], i, nm1);
+                            s[m] = negative_in(c, ws[m], i);
                             if (m < nm) ys[m] = __ldg(a.pos + s[m]);
                         }
 #pragma unroll
@@ -300,19 +451,32 @@ __global__ void __launch_bounds__(256) sync_chunk_kernel(const SyncArgs a) {
 }
 
 // y += eta * D * 2^-32 (optionally clipped to length `limit`), then D = 0.
+template <bool MULTI>
 __global__ void __launch_bounds__(256) sync_apply_kernel(float2 *pos, long long *disp, int32_t n, float eta,
-                                                         float limit, uint32_t *status) {
+                                                         float limit, uint32_t *status, const int32_t *node_graph,
+                                                         const GraphInfo *graphs, int32_t tick, float cap) {
     uint32_t flags = 0;
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         longlong2 *dp = reinterpret_cast<longlong2 *>(disp) + i;
         const longlong2 d = *dp;
-        float sx = eta * (__ll2float_rn(d.x) * kFixInv);
-        float sy = eta * (__ll2float_rn(d.y) * kFixInv);
-        if (limit > 0.0f) {
+        float eta_i = eta, limit_i = limit;
+        if (MULTI) {
+            const GraphInfo gi = graphs[node_graph[i]];
+            const int32_t t = tick - gi.start_tick;
+            if (t < 0 || t >= gi.total_epochs) {
+                *dp = make_longlong2(0, 0);
+                continue;
+            }
+            eta_i = schedule_eta(gi, t);
+            limit_i = cap > 0.0f ? (float)((double)cap * (double)eta_i / gi.eta0) : 0.0f;
+        }
+        float sx = eta_i * (__ll2float_rn(d.x) * kFixInv);
+        float sy = eta_i * (__ll2float_rn(d.y) * kFixInv);
+        if (limit_i > 0.0f) {
             const float len = sqrtf(sx * sx + sy * sy);
-            if (len > limit) {
-                const float sc = limit / len;
+            if (len > limit_i) {
+                const float sc = limit_i / len;
                 sx *= sc;
                 sy *= sc;
             }
@@ -329,63 +493,112 @@ __global__ void __launch_bounds__(256) sync_apply_kernel(float2 *pos, long long 
 
 }  // namespace
 
+template <bool RED>
+static cudaError_t launch_multi_g(const MultiArgs &a, int grid, int block, cudaStream_t s) {
+    switch (a.k < 4 ? a.k : 4) {
+        case 0: multi_epoch_kernel<RED, 0><<<grid, block, 0, s>>>(a); break;
+        case 1: multi_epoch_kernel<RED, 1><<<grid, block, 0, s>>>(a); break;
+        case 2: multi_epoch_kernel<RED, 2><<<grid, block, 0, s>>>(a); break;
+        case 3: multi_epoch_kernel<RED, 3><<<grid, block, 0, s>>>(a); break;
+        default: multi_epoch_kernel<RED, 4><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multi_epoch(const MultiArgs &a, int red_mode, int grid, int block, cudaStream_t s) {
+    return red_mode ? launch_multi_g<true>(a, grid, block, s) : launch_multi_g<false>(a, grid, block, s);
+}
+
+template <bool RED, int G>
+static int multi_occupancy(int block) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, multi_epoch_kernel<RED, G>, block, 0);
+    return nb > 0 ? nb : 1;
+}
+
+int multi_blocks_per_sm(int red_mode, int k, int block) {
+    const int g = k < 4 ? k : 4;
+    if (red_mode) {
+        switch (g) {
+            case 0: return multi_occupancy<true, 0>(block);
+            case 1: return multi_occupancy<true, 1>(block);
+            case 2: return multi_occupancy<true, 2>(block);
+            case 3: return multi_occupancy<true, 3>(block);
+            default: return multi_occupancy<true, 4>(block);
+        }
+    }
+    switch (g) {
+        case 0: return multi_occupancy<false, 0>(block);
+        case 1: return multi_occupancy<false, 1>(block);
+        case 2: return multi_occupancy<false, 2>(block);
+        case 3: return multi_occupancy<false, 3>(block);
+        default: return multi_occupancy<false, 4>(block);
+    }
+}
+
 cudaError_t launch_sync_chunk(const SyncArgs &a, int grid, int block, cudaStream_t s) {
-    sync_chunk_kernel<<<grid, block, 0, s>>>(a);
+    if (a.graphs)
+        sync_chunk_kernel<true><<<grid, block, 0, s>>>(a);
+    else
+        sync_chunk_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sync_apply(float2 *pos, long long *disp, int32_t n, float eta, float limit,
-                              uint32_t *status, int grid, int block, cudaStream_t s) {
-    sync_apply_kernel<<<grid, block, 0, s>>>(pos, disp, n, eta, limit, status);
+                              uint32_t *status, int grid, int block, cudaStream_t s, const int32_t *node_graph,
+                              const GraphInfo *graphs, int32_t tick, float cap) {
+    if (graphs)
+        sync_apply_kernel<true><<<grid, block, 0, s>>>(pos, disp, n, eta, limit, status, node_graph, graphs, tick, cap);
+    else
+        sync_apply_kernel<false><<<grid, block, 0, s>>>(pos, disp, n, eta, limit, status, nullptr, nullptr, 0, 0.0f);
     return cudaGetLastError();
 }
 
-template <bool RED>
+template <bool RED, bool MULTI>
 static cudaError_t launch_oriented_g(const OrientedArgs &a, int grid, int block, cudaStream_t s) {
     switch (a.k < 4 ? a.k : 4) {
-        case 0: oriented_epoch_kernel<RED, 0><<<grid, block, 0, s>>>(a); break;
-        case 1: oriented_epoch_kernel<RED, 1><<<grid, block, 0, s>>>(a); break;
-        case 2: oriented_epoch_kernel<RED, 2><<<grid, block, 0, s>>>(a); break;
-        case 3: oriented_epoch_kernel<RED, 3><<<grid, block, 0, s>>>(a); break;
-        default: oriented_epoch_kernel<RED, 4><<<grid, block, 0, s>>>(a); break;
+        case 0: oriented_epoch_kernel<RED, 0, MULTI><<<grid, block, 0, s>>>(a); break;
+        case 1: oriented_epoch_kernel<RED, 1, MULTI><<<grid, block, 0, s>>>(a); break;
+        case 2: oriented_epoch_kernel<RED, 2, MULTI><<<grid, block, 0, s>>>(a); break;
+        case 3: oriented_epoch_kernel<RED, 3, MULTI><<<grid, block, 0, s>>>(a); break;
+        default: oriented_epoch_kernel<RED, 4, MULTI><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s) {
-    return red_mode ? launch_oriented_g<true>(a, grid, block, s) : launch_oriented_g<false>(a, grid, block, s);
+    const bool multi = a.graphs != nullptr;
+    if (red_mode)
+        return multi ? launch_oriented_g<true, true>(a, grid, block, s) : launch_oriented_g<true, false>(a, grid, block, s);
+    return multi ? launch_oriented_g<false, true>(a, grid, block, s) : launch_oriented_g<false, false>(a, grid, block, s);
 }
 
-template <bool RED, int G>
+template <bool RED, int G, bool MULTI>
 static int oriented_occupancy(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, oriented_epoch_kernel<RED, G>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, oriented_epoch_kernel<RED, G, MULTI>, block, 0);
     return nb > 0 ? nb : 1;
 }
 
-int oriented_blocks_per_sm(int red_mode, int k, int block) {
-    const int g = k < 4 ? k : 4;
-    if (red_mode) {
-        switch (g) {
-            case 0: return oriented_occupancy<true, 0>(block);
-            case 1: return oriented_occupancy<true, 1>(block);
-            case 2: return oriented_occupancy<true, 2>(block);
-            case 3: return oriented_occupancy<true, 3>(block);
-            default: return oriented_occupancy<true, 4>(block);
-        }
+template <bool RED, bool MULTI>
+static int oriented_occupancy_k(int k, int block) {
+    switch (k < 4 ? k : 4) {
+        case 0: return oriented_occupancy<RED, 0, MULTI>(block);
+        case 1: return oriented_occupancy<RED, 1, MULTI>(block);
+        case 2: return oriented_occupancy<RED, 2, MULTI>(block);
+        case 3: return oriented_occupancy<RED, 3, MULTI>(block);
+        default: return oriented_occupancy<RED, 4, MULTI>(block);
     }
-    switch (g) {
-        case 0: return oriented_occupancy<false, 0>(block);
-        case 1: return oriented_occupancy<false, 1>(block);
-        case 2: return oriented_occupancy<false, 2>(block);
-        case 3: return oriented_occupancy<false, 3>(block);
-        default: return oriented_occupancy<false, 4>(block);
-    }
+}
+
+int oriented_blocks_per_sm(int red_mode, int k, int block, int multi) {
+    if (red_mode) return multi ? oriented_occupancy_k<true, true>(k, block) : oriented_occupancy_k<true, false>(k, block);
+    return multi ? oriented_occupancy_k<false, true>(k, block) : oriented_occupancy_k<false, false>(k, block);
 }
 
 int sync_blocks_per_sm(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sync_chunk_kernel, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sync_chunk_kernel<false>, block, 0);
     return nb > 0 ? nb : 1;
 }
 

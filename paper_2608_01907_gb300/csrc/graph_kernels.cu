@@ -33,7 +33,7 @@ __global__ void segment_rows_kernel(const int64_t *__restrict__ row_ptr, int32_t
 
 __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                     const int32_t *__restrict__ seg_row, int32_t n, int64_t nnz,
-                                    int32_t seg_len, uint32_t *flags_out) {
+                                    int32_t seg_len, uint32_t *flags_out, const int32_t *__restrict__ node_graph) {
     const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t flags = 0;
@@ -55,6 +55,7 @@ __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const i
                 continue;
             }
             if (j == row) flags |= kSelfLoop;
+            if (node_graph && node_graph[j] != node_graph[row]) flags |= kCrossGraph;
             if (e > row_begin && col_idx[e - 1] >= j) flags |= kUnsorted;
             // symmetry: binary search for `row` in row j
             int64_t lo = row_ptr[j], hi = row_ptr[j + 1];
@@ -264,6 +265,40 @@ __global__ void __launch_bounds__(kPairTile) objective_pairs_exact_kernel(const 
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+// Batch: per vertex i, (1 / (2 (n_g - 1))) * sum over j != i of its graph of
+// (d_i + d_j) U^r(r_ij); one thread per vertex, the graph's vertices in turn.
+__global__ void objective_pairs_batch_kernel(const float2 *__restrict__ pos, const int32_t *__restrict__ deg,
+                                             const int32_t *__restrict__ node_graph,
+                                             const GraphInfo *__restrict__ graphs, int32_t n, double *partial) {
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const GraphInfo gi = graphs[node_graph[i]];
+        if (gi.n < 2) continue;
+        const float2 yi = pos[i];
+        const float di = (float)deg[i];
+        double sum = 0.0;
+        float part = 0.0f;
+        int cnt = 0;
+        for (int32_t j = gi.node_base; j < gi.node_base + gi.n; ++j) {
+            if (j == i) continue;
+            const float2 yj = pos[j];
+            const float dx = yi.x - yj.x, dy = yi.y - yj.y;
+            const float r2 = fmaf(dx, dx, dy * dy);
+            part += (di + (float)deg[j]) * (0.5f * __frcp_rn(1.0f + r2));
+            if (++cnt == 256) {
+                sum += (double)part;
+                part = 0.0f;
+                cnt = 0;
+            }
+        }
+        sum += (double)part;
+        acc += sum / (2.0 * (double)(gi.n - 1));
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 // Sampled unordered pairs: p -> Philox(ctr = (p_lo, p_hi, 0xFFFFFFFD, 0), key = seed);
 // i = floor(w0 n / 2^32), j = negative(w1) of i.  Returns sum of (d_i + d_j) U^r.
 __global__ void objective_pairs_sampled_kernel(const float2 *__restrict__ pos, const int32_t *__restrict__ deg,
@@ -306,13 +341,14 @@ cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, 
 }
 
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s) {
+                                int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s,
+                                const int32_t *node_graph) {
     const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
     if (num_segs <= 0) return cudaSuccess;
     const int block = 256;
     const int64_t want = (num_segs + block - 1) / block;
     const int grid = (int)(want < 65536 ? want : 65536);
-    validate_csr_kernel<<<grid, block, 0, s>>>(row_ptr, col_idx, seg_row, n, nnz, seg_len, flags);
+    validate_csr_kernel<<<grid, block, 0, s>>>(row_ptr, col_idx, seg_row, n, nnz, seg_len, flags, node_graph);
     return cudaGetLastError();
 }
 
@@ -364,6 +400,13 @@ cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int
 cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n, double *partial,
                                          int grid, cudaStream_t s) {
     objective_pairs_exact_kernel<<<grid, kPairTile, 0, s>>>(pos, deg, n, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const int32_t *node_graph,
+                                         const GraphInfo *graphs, int32_t n, double *partial, int grid,
+                                         cudaStream_t s) {
+    objective_pairs_batch_kernel<<<grid, 256, 0, s>>>(pos, deg, node_graph, graphs, n, partial);
     return cudaGetLastError();
 }
 

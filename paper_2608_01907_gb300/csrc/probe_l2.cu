@@ -18,6 +18,8 @@
 //   op 8: load slot s, atomic add of a value depending on it into slot s
 //   op 9: load slot s of the lower half, atomic add of a dependent value
 //         into slot s of the upper half (reads and writes never alias)
+//   op 10: as op 8 with the load on the non-coherent path (ld.global.nc)
+//   op 11: as op 1 with the load on the non-coherent path (ld.global.nc)
 // with `depth` independent accesses in flight per thread.  Slots come from a
 // 64-bit mixing hash of (thread, iteration), so no random-number state is
 // carried.  The result is accesses per second measured by CUDA events.
@@ -50,7 +52,10 @@ __global__ void __launch_bounds__(256) probe_kernel(float2 *a, uint32_t n, int i
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) s[d] = s[d] % half;
         }
-        if (OP == 0 || OP == 1 || OP == 2 || OP == 4 || OP == 7 || OP == 8 || OP == 9) {
+        if (OP == 10 || OP == 11) {
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) v[d] = __ldg(a + s[d]);
+        } else if (OP == 0 || OP == 1 || OP == 2 || OP == 4 || OP == 7 || OP == 8 || OP == 9) {
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) v[d] = __ldcg(a + s[d]);
         } else {
@@ -61,13 +66,13 @@ __global__ void __launch_bounds__(256) probe_kernel(float2 *a, uint32_t n, int i
         for (int d = 0; d < DEPTH; ++d) {
             if (OP == 0) {
                 acc += v[d].x;
-            } else if (OP == 1 || OP == 6) {
+            } else if (OP == 1 || OP == 6 || OP == 11) {
                 v[d].x += 1e-7f;
                 __stcg(a + s[d], v[d]);
             } else if (OP == 7) {
                 v[d].x += 1e-7f;
                 __stcg(a + mix_slot(((tid << 20) ^ ((uint64_t)it * DEPTH + d)) + 0x51ull, n), v[d]);
-            } else if (OP == 8) {
+            } else if (OP == 8 || OP == 10) {
                 atomicAdd(a + s[d], make_float2(v[d].x * 1e-7f, 0.f));
             } else if (OP == 9) {
                 atomicAdd(a + s[d] + half, make_float2(v[d].x * 1e-7f, 0.f));
@@ -102,7 +107,7 @@ cudaError_t launch_op(int depth, float2 *a, uint32_t n, int iters, float *sink, 
 // load and/or write), or a negative value on error.
 extern "C" double snap_probe_random_access(float *a, uint32_t n, int op, int depth, int iters, int grid,
                                            void *cuda_stream) {
-    if (!a || n < 2 || op < 0 || op > 9 || iters <= 0 || grid <= 0) return -1.0;
+    if (!a || n < 2 || op < 0 || op > 11 || iters <= 0 || grid <= 0) return -1.0;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     float *sink = nullptr;
     if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) return -2.0;
@@ -123,7 +128,9 @@ extern "C" double snap_probe_random_access(float *a, uint32_t n, int op, int dep
             case 6: err = launch_op<6>(depth, p, n, iters, sink, grid, s); break;
             case 7: err = launch_op<7>(depth, p, n, iters, sink, grid, s); break;
             case 8: err = launch_op<8>(depth, p, n, iters, sink, grid, s); break;
-            default: err = launch_op<9>(depth, p, n, iters, sink, grid, s); break;
+            case 9: err = launch_op<9>(depth, p, n, iters, sink, grid, s); break;
+            case 10: err = launch_op<10>(depth, p, n, iters, sink, grid, s); break;
+            default: err = launch_op<11>(depth, p, n, iters, sink, grid, s); break;
         }
     }
     cudaEventRecord(e1, s);

@@ -19,6 +19,7 @@ enum : uint32_t {
     kSelfLoop = 2u,       // j == i
     kUnsorted = 4u,       // row not strictly ascending (duplicate or unsorted)
     kAsymmetric = 8u,     // (i, j) present but (j, i) missing
+    kCrossGraph = 16u,    // an edge joins two graphs of a batch
 };
 
 // t-FDP constants (Section 3.1: alpha = 0.1, beta = 8, gamma = 2).
@@ -29,6 +30,25 @@ constexpr float kBeta = 8.0f;
 constexpr float kFixScale = 4294967296.0f;
 constexpr float kFixInv = 2.3283064365386963e-10f;   // 2^-32
 constexpr float kFixClamp = 1048576.0f;              // |term| <= 2^20 before scaling
+
+// One graph of a batch: its vertices are [node_base, node_base + n), its
+// directed edges [edge_base, edge_base + 2|E_g|) of the batch CSR.  Random
+// words use the graph-local edge index and the graph's own seed, and the
+// graph runs epoch (tick - start_tick) of its own schedule, so its layout
+// draws exactly the numbers it would draw alone.  A graph is active while
+// 0 <= tick - start_tick < total_epochs.
+struct GraphInfo {
+    int32_t node_base;
+    int32_t n;
+    int64_t edge_base;
+    uint64_t seed;
+    int32_t start_tick;
+    int32_t total_epochs;
+    double eta0;
+    double eta_min;
+    int32_t kind;      // schedule kind (0: linear decay, 1: constant)
+    int32_t pad;
+};
 
 struct SyncArgs {
     const int64_t *row_ptr;
@@ -43,6 +63,8 @@ struct SyncArgs {
     uint32_t epoch;
     uint64_t seed;
     uint32_t *status;
+    const int32_t *node_graph;   // batch only
+    const GraphInfo *graphs;
 };
 
 // Oriented bundle list: entry p of row i is {j, CSR index of (i, j), CSR
@@ -59,24 +81,62 @@ struct OrientedArgs {
     int64_t perm_add;
     int32_t n;
     int32_t k;
-    uint32_t epoch;
+    uint32_t epoch;           // single graph: the epoch; batch: the tick
     uint64_t seed;
     float eta;
     uint32_t *status;
+    const int32_t *node_graph;   // batch only: graph of every vertex
+    const GraphInfo *graphs;     // batch only
+    float inflight_share;        // lanes in flight / segments (share of segments running at once)
 };
 
 cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s);
-int oriented_blocks_per_sm(int red_mode, int k, int block);
+
+// One job of a multi-handle epoch: a single-graph HOGWILD handle's device
+// arrays, its positions, and the epoch, step and seed it runs this launch.
+struct JobDesc {
+    const int64_t *row_ptr;
+    const int4 *ent;
+    const int4 *seg;
+    float2 *pos;
+    int64_t num_segs;
+    int64_t seg_prefix;     // segments of the jobs before this one
+    uint64_t seed;
+    int32_t n;
+    uint32_t epoch;
+    float eta;
+    int32_t pad[3];
+};
+
+struct MultiArgs {
+    const JobDesc *jobs;
+    int32_t num_jobs;
+    int32_t k;
+    int64_t total_segs;
+    int64_t perm_mul;         // segment order: (perm_mul * w + perm_add) mod total_segs
+    int64_t perm_add;
+    uint32_t *status;
+    float inflight_share;
+};
+
+cudaError_t launch_multi_epoch(const MultiArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+int multi_blocks_per_sm(int red_mode, int k, int block);
+int oriented_blocks_per_sm(int red_mode, int k, int block, int multi);
 cudaError_t launch_sync_chunk(const SyncArgs &a, int grid, int block, cudaStream_t s);
+// y += eta * D * 2^-32 (clipped to `limit` when > 0), D = 0.  For a batch
+// (graphs != nullptr) eta and the clip come from each vertex's graph at
+// `tick`, with limit = cap * eta_t / eta0 when cap > 0.
 cudaError_t launch_sync_apply(float2 *pos, long long *disp, int32_t n, float eta, float limit,
-                              uint32_t *status, int grid, int block, cudaStream_t s);
+                              uint32_t *status, int grid, int block, cudaStream_t s,
+                              const int32_t *node_graph = nullptr, const GraphInfo *graphs = nullptr,
+                              int32_t tick = 0, float cap = 0.0f);
 int sync_blocks_per_sm(int block);
 
 cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, int32_t seg_len,
                                 int32_t *seg_row, int64_t num_segs, cudaStream_t s);
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags,
-                                cudaStream_t s);
+                                cudaStream_t s, const int32_t *node_graph = nullptr);
 // Construction of the oriented bundle list (flags, exclusive scan, scatter, offsets).
 cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 const int32_t *deg, int64_t nnz, int32_t seg_len, int32_t *flags, cudaStream_t s);
@@ -95,6 +155,11 @@ cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, c
                                       const float2 *pos, double *partial, int grid, cudaStream_t s);
 cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n,
                                          double *partial, int grid, cudaStream_t s);
+// Batch: sum over graphs of (1 / (2 (n_g - 1))) * sum over ordered pairs of the
+// graph of (d_i + d_j) U^r; the host applies k / 2.
+cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const int32_t *node_graph,
+                                         const GraphInfo *graphs, int32_t n, double *partial, int grid,
+                                         cudaStream_t s);
 cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, int32_t n,
                                            int64_t pairs, uint64_t seed, double *partial, int grid,
                                            cudaStream_t s);

@@ -10,7 +10,8 @@ import ctypes
 from . import _build
 
 OPS = {"load": 0, "load_store": 1, "load_atomic": 2, "atomic": 3, "load_exch": 4, "exch": 5, "store": 6,
-       "load_store_other": 7, "load_dep_atomic": 8, "load_dep_atomic_other": 9}
+       "load_store_other": 7, "load_dep_atomic": 8, "load_dep_atomic_other": 9,
+       "ldnc_dep_atomic": 10, "ldnc_store": 11}
 _lib = None
 
 

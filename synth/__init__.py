@@ -12,6 +12,8 @@ from .graphs import (  # noqa: F401
     lfr_graph,
     rmat_graph,
     batch_sbm_graphs,
+    planted_partition_graph,
+    serving_graph_pool,
     initial_positions,
     tiny_graph,
 )

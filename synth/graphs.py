@@ -266,37 +266,59 @@ def rmat_graph(scale: int = 22, num_edges: int = 34_000_000, a: float = 0.57, b:
                  meta=dict(a=a, b=b, c=c, d=1 - a - b - c, seed=seed))
 
 
+def planted_partition_graph(n: int, communities: int, avg_degree: float, mu: float, rng: np.random.Generator,
+                            name: str = "") -> Graph:
+    """Planted-partition graph drawn as uniform random pairs: a share 1 - mu
+    of the n * avg_degree / 2 edges joins two vertices of one community
+    (chosen with probability proportional to its pair count), the rest two
+    uniform vertices; duplicates and self-loops are removed."""
+    communities = max(1, min(communities, n // 4 if n >= 8 else 1))
+    m = int(round(n * avg_degree / 2))
+    labels = (np.arange(n) * communities // n).astype(np.int32)
+    starts = np.searchsorted(labels, np.arange(communities))
+    sizes = np.diff(np.append(starts, n))
+    m_in = int(round(m * (1 - mu)))
+    w = sizes.astype(np.float64) ** 2
+    comm = rng.choice(communities, size=m_in, p=w / w.sum())
+    u_in = starts[comm] + (rng.random(m_in) * sizes[comm]).astype(np.int64)
+    v_in = starts[comm] + (rng.random(m_in) * sizes[comm]).astype(np.int64)
+    m_out = m - m_in
+    u_out = rng.integers(0, n, m_out)
+    v_out = rng.integers(0, n, m_out)
+    row_ptr, col_idx = edges_to_csr(n, np.concatenate([u_in, u_out]), np.concatenate([v_in, v_out]))
+    return Graph(n, row_ptr, col_idx, labels=labels, name=name)
+
+
 def batch_sbm_graphs(count: int = 4096, nmin: int = 100, nmax: int = 20_000, cmin: int = 4,
                      cmax: int = 32, dmin: float = 6.0, dmax: float = 20.0, mu: float = 0.1,
                      seed: int = 1) -> list[Graph]:
-    """Many small planted-partition graphs (log-uniform sizes).
-
-    Each graph has U{cmin..cmax} equal-ish communities and mean degree
-    U[dmin, dmax]; a fraction mu of the edges join different communities.
-    Edges are drawn as uniform random pairs (internal ones within a random
-    community weighted by its pair count), then de-duplicated.
-    """
+    """Many small planted-partition graphs: n log-uniform in [nmin, nmax],
+    U{cmin..cmax} communities, mean degree U[dmin, dmax], mixing mu."""
     rng = _rng(seed, 51)
     out = []
     for g in range(count):
         n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
         ncomm = int(rng.integers(cmin, cmax + 1))
-        ncomm = max(1, min(ncomm, n // 4))
         avg = rng.uniform(dmin, dmax)
-        m = int(round(n * avg / 2))
-        labels = (np.arange(n) * ncomm // n).astype(np.int32)
-        starts = np.searchsorted(labels, np.arange(ncomm))
-        sizes = np.diff(np.append(starts, n))
-        m_in = int(round(m * (1 - mu)))
-        w = sizes.astype(np.float64) ** 2
-        comm = rng.choice(ncomm, size=m_in, p=w / w.sum())
-        u_in = starts[comm] + (rng.random(m_in) * sizes[comm]).astype(np.int64)
-        v_in = starts[comm] + (rng.random(m_in) * sizes[comm]).astype(np.int64)
-        m_out = m - m_in
-        u_out = rng.integers(0, n, m_out)
-        v_out = rng.integers(0, n, m_out)
-        row_ptr, col_idx = edges_to_csr(n, np.concatenate([u_in, u_out]), np.concatenate([v_in, v_out]))
-        out.append(Graph(n, row_ptr, col_idx, labels=labels, name=f"bsbm-{g}"))
+        out.append(planted_partition_graph(n, ncomm, avg, mu, rng, name=f"bsbm-{g}"))
+    return out
+
+
+def serving_graph_pool(count: int = 48, emin: int = 1_000, emax: int = 2_000_000, seed: int = 1) -> list[Graph]:
+    """Graphs for the serving workload: half R-MAT (a, b, c = .57, .19, .19;
+    n = 2^ceil(log2(|E|/4))), half 8-community planted partitions (n = |E|/5,
+    mixing 0.1); |E| log-uniform in [emin, emax]."""
+    rng = _rng(seed, 71)
+    out = []
+    for q in range(count):
+        e = int(np.exp(rng.uniform(np.log(emin), np.log(emax))))
+        if q % 2 == 0:
+            scale = max(4, int(np.ceil(np.log2(max(e / 4, 2)))))
+            out.append(rmat_graph(scale=scale, num_edges=min(e, (1 << scale) * ((1 << scale) - 1) // 4),
+                                  seed=seed * 1000 + q))
+        else:
+            n = max(16, e // 5)
+            out.append(planted_partition_graph(n, 8, 2 * e / n, 0.1, rng, name=f"pp-{q}"))
     return out
 
 

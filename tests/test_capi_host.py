@@ -47,10 +47,11 @@ def test_struct_layouts_match_header(lib):
 #include <stddef.h>
 #include "snap_layout.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(snap_schedule), offsetof(snap_schedule, eta0),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(snap_schedule), offsetof(snap_schedule, eta0),
          offsetof(snap_schedule, eta_min), sizeof(snap_options), offsetof(snap_options, node_weights),
          offsetof(snap_options, sync_substeps), offsetof(snap_options, sync_cap),
-         offsetof(snap_options, block_threads));
+         offsetof(snap_options, block_threads), offsetof(snap_options, flags), SNAP_FLAG_CUDA_GRAPH);
+  printf("%zu\n", offsetof(snap_options, max_inflight));
   return 0;
 }
 '''
@@ -62,12 +63,14 @@ int main(void) {
         vals = [int(v) for v in subprocess.check_output([exe]).split()]
     S, O = snap.SnapSchedule, snap.SnapOptions
     assert vals == [ctypes.sizeof(S), S.eta0.offset, S.eta_min.offset, ctypes.sizeof(O), O.node_weights.offset,
-                    O.sync_substeps.offset, O.sync_cap.offset, O.block_threads.offset]
+                    O.sync_substeps.offset, O.sync_cap.offset, O.block_threads.offset, O.flags.offset,
+                    snap.FLAG_CUDA_GRAPH, O.max_inflight.offset]
 
 
 def test_options_default(lib):
     o = snap.snap_options_default()
-    assert (o.mode, o.sampler, o.sync_substeps, o.sync_cap, o.segment_edges, o.block_threads) == (0, 0, 1, 0.0, 0, 0)
+    assert (o.mode, o.sampler, o.sync_substeps, o.sync_cap, o.segment_edges, o.block_threads, o.flags) == \
+        (0, 0, 1, 0.0, 0, 0, 0)
 
 
 def _status(fn, *a, **kw):
@@ -94,9 +97,12 @@ def test_host_side_argument_errors(lib):
     o = snap.make_options(sampler=snap.SAMPLER_DEGREE)
     assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)[0] == 5
     for bad in (dict(mode=7), dict(sync_substeps=0), dict(segment_edges=6), dict(block_threads=48),
-                dict(sync_cap=-1.0), dict(block_threads=512)):
+                dict(sync_cap=-1.0), dict(block_threads=512), dict(max_inflight=1.5)):
         assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=snap.make_options(**bad))[0] == 1, bad
-    assert "snap_layout" not in snap.snap_last_error() or True
+    o = snap.make_options()
+    o.flags = 6
+    st, msg = _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)
+    assert st == 1 and "flags" in msg
 
 
 def test_null_handle_errors(lib):
