@@ -102,9 +102,11 @@ typedef struct {
     const float *node_weights;/* host, n; SNAP_SAMPLER_WEIGHTS only (unused now) */
     int32_t sync_substeps;    /* S >= 1 row chunks per epoch in SNAP_MODE_SYNC */
     float sync_cap;           /* > 0: clip each node's sync step to cap*eta_t/eta0 */
-    int32_t segment_edges;    /* work per lane segment, a multiple of 4 in [4, 4096]: oriented entries
-                                 (2 directed edges each) in the HOGWILD modes, directed edges in SYNC;
-                                 0 = default (HOGWILD: 4; SYNC: 32) */
+    int32_t segment_edges;    /* work per lane segment, a multiple of 4 in [4, 4096]: in the HOGWILD
+                                 modes the length of a chunk of the oriented list (entries of 2
+                                 directed edges each; a chunk may span rows, and a graph with at most
+                                 this many entries is one chunk, so one lane); in SYNC directed
+                                 edges; 0 = default (HOGWILD: 4; SYNC: 32) */
     int32_t block_threads;    /* threads per block; 0 = default (256) */
     int32_t flags;            /* SNAP_FLAG_* bits */
     float max_inflight;       /* HOGWILD: at most this share of the graph's entries in flight at once
@@ -222,7 +224,7 @@ snap_status snap_layout_check(snap_layout_t h, void *cuda_stream);
 int64_t snap_layout_device_bytes(snap_layout_t h);
 
 /*
- * snap_layout_autotune -- choose the segment size (bundle entries per lane)
+ * snap_layout_autotune -- choose the chunk size (oriented entries per lane)
  * and the block size of a HOGWILD handle by timing epochs.  Candidates are
  * 4, 8, 16, 32 entries x 128/256 threads, all under the handle's
  * max_inflight bound (max_inflight here is unused and kept for the ABI).  The

@@ -168,16 +168,16 @@ struct snap_layout {
     int32_t *d_deg = nullptr;
     long long *d_disp = nullptr;
     // oriented bundle list (HOGWILD modes): one entry per undirected edge,
-    // whole rows packed into segments of about act_seg_len entries
+    // cut into chunks of act_seg_len entries stored in slot order (ChunkLayout)
     int64_t act_nnz = 0;
     int64_t act_num_segs = 0;
     int32_t act_seg_len = 32;
-    int64_t perm_mul = 1;
+    ChunkLayout act_layout{0, 0, 0, 0};   // T == 0 while the list is still row-major
+    int64_t perm_mul = 1;                 // slot-group order multiplier
     int64_t *d_act_row_ptr = nullptr;
     int4 *d_act_ent = nullptr;
-    int4 *d_act_seg = nullptr;
-    size_t act_seg_capacity = 0;
-    std::vector<int64_t> act_rp_host;   // host copy of the oriented row offsets (for repacking)
+    int2 *d_act_meta = nullptr;
+    int64_t act_ent_bytes = 0, act_meta_bytes = 0;
     // batch of graphs (num_graphs > 1): graph of every vertex and per-graph table
     int32_t num_graphs = 1;
     std::vector<int32_t> graph_offsets;   // num_graphs + 1 vertex offsets
@@ -234,14 +234,14 @@ struct snap_layout {
         release_csr();
         free_async(d_act_row_ptr);
         free_async(d_act_ent);
-        free_async(d_act_seg);
+        free_async(d_act_meta);
         free_async(d_node_graph);
         free_async(d_graphs);
         d_node_graph = nullptr;
         d_graphs = nullptr;
         d_act_row_ptr = nullptr;
         d_act_ent = nullptr;
-        d_act_seg = nullptr;
+        d_act_meta = nullptr;
         free_async(d_deg);
         free_async(d_disp);
         free_async(d_status);
@@ -278,77 +278,52 @@ static int64_t gcd64(int64_t a, int64_t b) {
     return a;
 }
 
-// Segments of the oriented list: whole rows packed greedily up to `target`
-// entries; a row longer than `target` is cut into equal pieces.
-static void pack_segments(const std::vector<int64_t> &rp, int32_t target, const std::vector<int32_t> &graph_offsets,
-                          std::vector<int4> &out) {
-    out.clear();
-    const int32_t n = (int32_t)rp.size() - 1;
-    int64_t open_begin = -1, open_end = 0;
-    int32_t open_row = 0;
-    size_t next_graph = 1;   // segments never span two graphs of a batch
-    auto close = [&]() {
-        if (open_begin >= 0) out.push_back(make_int4((int)open_begin, (int)open_end, open_row, 1));
-        open_begin = -1;
-    };
-    for (int32_t i = 0; i < n; ++i) {
-        while (next_graph < graph_offsets.size() && graph_offsets[next_graph] <= i) {
-            close();
-            ++next_graph;
-        }
-        const int64_t len = rp[(size_t)i + 1] - rp[(size_t)i];
-        if (len == 0) continue;
-        if (len > target) {
-            close();
-            const int64_t pieces = (len + target - 1) / target;
-            for (int64_t q = 0; q < pieces; ++q) {
-                const int64_t b = rp[(size_t)i] + len * q / pieces;
-                const int64_t e = rp[(size_t)i] + len * (q + 1) / pieces;
-                out.push_back(make_int4((int)b, (int)e, i, (int)pieces));
-            }
-            continue;
-        }
-        if (open_begin >= 0 && open_end - open_begin + len > target) close();
-        if (open_begin < 0) {
-            open_begin = rp[(size_t)i];
-            open_row = i;
-        }
-        open_end = rp[(size_t)i + 1];
-    }
-    close();
+// Multiplier coprime with m near its golden section (0 when m <= 1): an
+// affine map with it sends neighbouring indices far apart.
+static int64_t golden_multiplier(int64_t m) {
+    if (m <= 1) return 0;
+    int64_t x = (int64_t)(0.6180339887498949 * (double)m) | 1;
+    while (gcd64(x, m) != 1) x += 2;
+    x %= m;
+    return x == 0 ? 1 : x;
 }
 
-// (Re)packs the oriented list into segments of about `target` entries and
-// uploads them; the segment array only grows.
+// (Re)cuts the oriented list into chunks of `target` entries: the entries
+// move from the current layout (row-major right after construction) into a
+// fresh array in the new slot order, and the slot table is rebuilt.
 static cudaError_t set_segments(snap_layout *h, AllocCounter &ac, int32_t target, cudaStream_t stream) {
-    std::vector<int4> segs;
-    pack_segments(h->act_rp_host, target, h->graph_offsets, segs);
-    cudaError_t err = cudaSuccess;
-    if (segs.size() > h->act_seg_capacity || !h->d_act_seg) {
-        int4 *fresh = nullptr;
-        const size_t cap = segs.empty() ? 1 : segs.size();
-        err = dev_alloc(ac, (void **)&fresh, sizeof(int4) * cap, stream);
-        if (err != cudaSuccess) return err;
-        if (h->d_act_seg) {
-            cudaFreeAsync(h->d_act_seg, stream);
-            h->device_bytes -= (int64_t)(sizeof(int4) * h->act_seg_capacity);
-        }
-        h->d_act_seg = fresh;
-        h->act_seg_capacity = cap;
-        h->device_bytes += (int64_t)(sizeof(int4) * cap);
+    if (h->act_nnz > 0 && target > h->act_nnz) target = (int32_t)h->act_nnz;   // one chunk
+    if (h->last_use) cudaStreamWaitEvent(stream, h->last_use, 0);   // the old arrays' last readers
+    ChunkLayout to;
+    to.T = target;
+    to.S = (h->act_nnz + target - 1) / target;
+    to.mul = golden_multiplier(to.S);
+    to.add = to.S > 1 ? to.S / 3 : 0;
+    const int64_t ent_bytes = (int64_t)sizeof(int4) * (to.S > 0 ? to.S * (int64_t)target : 1);
+    const int64_t meta_bytes = (int64_t)sizeof(int2) * (to.S > 0 ? to.S : 1);
+    int4 *ent = nullptr;
+    int2 *meta = nullptr;
+    cudaError_t err = dev_alloc(ac, (void **)&ent, (size_t)ent_bytes, stream);
+    if (err == cudaSuccess) err = dev_alloc(ac, (void **)&meta, (size_t)meta_bytes, stream);
+    if (err == cudaSuccess)
+        err = launch_chunk_layout(h->d_act_ent, h->act_layout, ent, to, meta, h->d_act_row_ptr, h->n, h->act_nnz,
+                                  stream);
+    if (err != cudaSuccess) {
+        if (ent) cudaFreeAsync(ent, stream);
+        if (meta) cudaFreeAsync(meta, stream);
+        return err;
     }
-    if (!segs.empty()) {
-        err = cudaMemcpyAsync(h->d_act_seg, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, stream);
-        if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
-        if (err != cudaSuccess) return err;
-    }
+    cudaFreeAsync(h->d_act_ent, stream);
+    if (h->d_act_meta) cudaFreeAsync(h->d_act_meta, stream);
+    h->device_bytes += ent_bytes + meta_bytes - h->act_ent_bytes - h->act_meta_bytes;
+    h->d_act_ent = ent;
+    h->d_act_meta = meta;
+    h->act_ent_bytes = ent_bytes;
+    h->act_meta_bytes = meta_bytes;
+    h->act_layout = to;
     h->act_seg_len = target;
-    h->act_num_segs = (int64_t)segs.size();
-    // segment order multiplier: coprime with the segment count, near its golden section
-    int64_t m = (int64_t)(0.6180339887498949 * (double)h->act_num_segs) | 1;
-    while (h->act_num_segs > 1 && gcd64(m, h->act_num_segs) != 1) m += 2;
-    h->perm_mul = h->act_num_segs > 1 ? m % h->act_num_segs : 0;
-    if (h->act_num_segs > 1 && h->perm_mul == 0) h->perm_mul = 1;
+    h->act_num_segs = to.S;
+    h->perm_mul = golden_multiplier((to.S + 31) / 32);
     return cudaSuccess;
 }
 
@@ -359,9 +334,9 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     const int64_t nnz = h->nnz;
     h->act_nnz = nnz / 2;   // symmetric and loop-free: each undirected edge once
     if (h->act_seg_len == 0) {
-        // Default segment size: 4 entries.  A lane applies a segment's steps
-        // of one source back to back; long bursts of one source's steps move
-        // the layout away from Algorithm 1's shuffled order (R-MAT 2^17,
+        // Default chunk: 4 entries.  A lane applies a chunk's steps of one
+        // source back to back; long bursts of one source's steps move the
+        // layout away from Algorithm 1's shuffled order (R-MAT 2^17,
         // sequential, eta0 = 1: +0.8% energy at 4 entries, +5% at 32, +10% at
         // 128).  Concurrency is bounded separately (max_inflight).
         h->act_seg_len = 4;
@@ -387,7 +362,8 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
         }
     };
     alloc((void **)&h->d_act_row_ptr, sizeof(int64_t) * ((size_t)n + 1), true, "oriented row offsets");
-    alloc((void **)&h->d_act_ent, sizeof(int4) * (size_t)(h->act_nnz > 0 ? h->act_nnz : 1), true, "oriented entries");
+    alloc((void **)&h->d_act_ent, sizeof(int4) * (size_t)(h->act_nnz > 0 ? h->act_nnz : 1), false,
+          "oriented entries");
     alloc((void **)&flags, sizeof(int32_t) * ((size_t)nnz + 1), false, "orientation flags");
     alloc((void **)&pos, sizeof(int32_t) * ((size_t)nnz + 1), false, "orientation offsets");
     if (err == cudaSuccess) step(exclusive_scan_i32(nullptr, &temp_bytes, flags, pos, nnz + 1, stream), "scan size");
@@ -400,23 +376,24 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
                                    h->d_act_ent, stream), "orientation scatter kernel");
         step(launch_orient_rowptr(h->d_row_ptr, pos, n, h->d_act_row_ptr, stream), "orientation offsets kernel");
     }
-    std::vector<int64_t> act_rp;
+    int64_t total = -1;
     if (err == cudaSuccess) {
-        act_rp.resize((size_t)n + 1);
-        step(cudaMemcpyAsync(act_rp.data(), h->d_act_row_ptr, sizeof(int64_t) * ((size_t)n + 1),
-                             cudaMemcpyDeviceToHost, stream), "read oriented row offsets");
+        step(cudaMemcpyAsync(&total, h->d_act_row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream),
+             "read oriented entry count");
         step(cudaStreamSynchronize(stream), "orientation");
     }
     if (flags) cudaFreeAsync(flags, stream);
     if (pos) cudaFreeAsync(pos, stream);
     if (temp) cudaFreeAsync(temp, stream);
     if (err != cudaSuccess) return cuda_fail(err, what);
-    if (act_rp[(size_t)n] != h->act_nnz)
-        return fail(SNAP_ERR_CUDA, "orientation produced %lld entries, expected %lld", (long long)act_rp[(size_t)n],
+    if (total != h->act_nnz)
+        return fail(SNAP_ERR_CUDA, "orientation produced %lld entries, expected %lld", (long long)total,
                     (long long)h->act_nnz);
-    h->act_rp_host = std::move(act_rp);
+    h->act_layout = ChunkLayout{0, 0, 0, 0};   // row-major
+    h->act_ent_bytes = 0;
     err = set_segments(h, ac, h->act_seg_len, stream);
-    if (err != cudaSuccess) return cuda_fail(err, "oriented segments");
+    if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+    if (err != cudaSuccess) return cuda_fail(err, "oriented chunks");
     h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
                                  sizeof(int32_t) * (size_t)(h->num_segs * h->seg_len + 4) +
                                  sizeof(int32_t) * (size_t)(h->num_segs > 0 ? h->num_segs : 1));
@@ -747,11 +724,14 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
             OrientedArgs a;
             a.row_ptr = h->d_act_row_ptr;
             a.ent = h->d_act_ent;
-            a.seg = h->d_act_seg;
+            a.meta = h->d_act_meta;
             a.pos = pos;
             a.num_segs = h->act_num_segs;
+            a.nnz = h->act_nnz;
+            a.seg_len = h->act_seg_len;
             a.perm_mul = h->perm_mul;
-            a.perm_add = (int64_t)(mix64(seed ^ (0x5EC0ull * (uint64_t)(t + 1))) % (uint64_t)h->act_num_segs);
+            a.perm_add = (int64_t)(mix64(seed ^ (0x5EC0ull * (uint64_t)(t + 1))) %
+                                   (uint64_t)(h->act_num_segs > 0 ? (h->act_num_segs + 31) / 32 : 1));
             a.n = h->n;
             a.k = neg_samples;
             a.epoch = (uint32_t)t;
@@ -908,7 +888,7 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
             err = launch_objective_edges(h->d_row_ptr, h->d_col, h->d_seg_row, pos, h->nnz, h->seg_len,
                                          h->d_partial, kObjGrid, stream);
         else if (h->act_num_segs > 0)
-            err = launch_objective_oriented(h->d_act_row_ptr, h->d_act_ent, h->d_act_seg, h->act_num_segs, pos,
+            err = launch_objective_oriented(h->d_act_row_ptr, h->d_act_ent, h->d_act_meta, h->act_layout, h->act_nnz, pos,
                                             h->d_partial, kObjGrid, stream);
     }
     if (h->num_graphs > 1 && !exact)
@@ -1166,9 +1146,11 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
         JobDesc &jd = m->h_jobs[used++];
         jd.row_ptr = h->d_act_row_ptr;
         jd.ent = h->d_act_ent;
-        jd.seg = h->d_act_seg;
+        jd.meta = h->d_act_meta;
         jd.pos = reinterpret_cast<float2 *>(positions[q]);
         jd.num_segs = h->act_num_segs;
+        jd.nnz = h->act_nnz;
+        jd.seg_len = h->act_seg_len;
         jd.seg_prefix = total;
         jd.seed = seeds[q];
         jd.n = h->n;
@@ -1189,11 +1171,9 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
     a.num_jobs = used;
     a.k = neg_samples;
     a.total_segs = total;
-    int64_t mul = (int64_t)(0.6180339887498949 * (double)total) | 1;
-    while (total > 1 && gcd64(mul, total) != 1) mul += 2;
-    a.perm_mul = total > 1 ? mul % total : 0;
-    if (total > 1 && a.perm_mul == 0) a.perm_mul = 1;
-    a.perm_add = (int64_t)(mixkey % (uint64_t)total);
+    const int64_t groups = (total + 31) / 32;
+    a.perm_mul = golden_multiplier(groups);
+    a.perm_add = (int64_t)(mixkey % (uint64_t)groups);
     a.status = m->d_status;
     const int g = neg_samples < 4 ? neg_samples : 4;
     if (m->grid[red][g] == 0) m->grid[red][g] = m->sms * multi_blocks_per_sm(red, neg_samples, 256);

@@ -4,12 +4,12 @@
 // HOGWILD modes work on oriented bundles (built by capi.cu at create):
 // every undirected edge {i, j} is listed once, in the row of its
 // higher-ranked endpoint (degree, then smaller id), with the CSR indices of
-// both directed copies.  Rows are packed whole into segments of about 32
-// entries (rows longer than that are cut into pieces); lane w of the grid
-// takes segment perm_t(w), an affine permutation of the segment ids that
-// changes every epoch (the shuffle before bundling of Section 3.4), keeps
-// the source y_i in registers while it walks its rows, and applies both
-// directed steps of every entry.
+// both directed copies.  The row-major list is cut into chunks of a few
+// entries, stored in a pseudo-random slot order; a warp takes one group of
+// 32 slots and the order of the groups is an affine permutation that changes
+// every epoch (the shuffle before bundling of Section 3.4).  A lane keeps
+// the source y_i of its current row in registers and applies both directed
+// steps of every entry.
 //
 // The synchronous mode walks the full CSR (all directed edges, row-major)
 // in fixed segments with positions frozen, accumulating int64 fixed-point
@@ -212,7 +212,7 @@ __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, const Grap
     apply_partner<RED>(a.pos, j, yj, make_float2(yj.x - yj0.x, yj.y - yj0.y));
 }
 
-// Source write-back at the end of a row run.
+// Source write-back at the end of a row's run in a chunk.
 // HOGWILD writes the lane's copy with an atomic exchange: the same
 // last-writer-wins result as a store, but a source cut into many pieces (a
 // hub) is written thousands of times per epoch, and L2 serialises plain
@@ -240,54 +240,84 @@ __device__ __forceinline__ void write_oriented_source(const OrientedArgs &a, int
 #define SNAP_ORIENTED_MIN_BLOCKS 1
 #endif
 
-// Segments never span two graphs of a batch, so the graph is looked up once
-// per segment.
+// Slot of lane w: the 32 lanes of a warp take the 32 slots of one slot group
+// (one 256-byte read of the slot table, one 512-byte read of entries per
+// entry step), and the order of the groups is an affine permutation that changes
+// every epoch.  The chunks were placed in slots by a fixed bijection at
+// create, so the slots of a group hold unrelated parts of the graph.
+__device__ __forceinline__ int64_t slot_of(int64_t w, int64_t groups, int64_t mul, int64_t add) {
+    const int64_t g = (int64_t)(((uint64_t)mul * (uint64_t)(w >> 5) + (uint64_t)add) % (uint64_t)groups);
+    return (g << 5) | (w & 31);
+}
+
+// Pieces of a row in the chunk cut: the chunks its entries fall in.
+__device__ __forceinline__ int row_pieces(int64_t row_begin, int64_t row_end, int32_t T) {
+    return (int)((uint32_t)(row_end - 1) / (uint32_t)T - (uint32_t)row_begin / (uint32_t)T) + 1;
+}
+
+// One chunk: the source y_i of the current row is held in registers and
+// written back when the walk leaves the row.
+template <bool RED, int G, bool MULTI>
+__device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t slot, uint32_t &flags) {
+    const int2 mt = __ldg(a.meta + slot);   // {row of the first entry, chunk}
+    int32_t row = mt.x;
+    int64_t p = (int64_t)mt.y * a.seg_len;
+    const int64_t p1 = p + a.seg_len < a.nnz ? p + a.seg_len : a.nnz;
+    int64_t row_begin = RED ? __ldg(a.row_ptr + row) : 0;
+    int64_t row_end = __ldg(a.row_ptr + row + 1);
+    const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
+    const int64_t step = chunk_group_width(slot, a.num_segs);
+    GraphCtx c = graph_ctx<MULTI>(a, row);
+    float2 yi = load_pos(a.pos + row);
+    float2 yi0 = yi;
+    for (; p < p1; ++p, ep += step) {
+        if (p >= row_end) {
+            if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
+                                                     flags);
+            do {
+                ++row;
+                row_begin = row_end;
+                row_end = __ldg(a.row_ptr + row + 1);
+            } while (row_end <= p);
+            if (MULTI) c = graph_ctx<MULTI>(a, row);
+            yi = load_pos(a.pos + row);
+            yi0 = yi;
+        }
+        if (!c.active) continue;
+        const int4 en = load_entry(ep);   // {j, index of (i, j), index of (j, i), -}
+        oriented_entry<RED, G>(a, c, row, en.x, en.y, en.z, yi);
+    }
+    if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
+                                             flags);
+}
+
+// In a batch a chunk may cross from one graph into the next; the graph is
+// looked up again at every row change.
 template <bool RED, int G, bool MULTI>
 __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_kernel(const OrientedArgs a) {
     uint32_t flags = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.num_segs; w += stride) {
-        const int64_t ws = (int64_t)(((uint64_t)a.perm_mul * (uint64_t)w + (uint64_t)a.perm_add) %
-                                     (uint64_t)a.num_segs);
-        const int4 sg = __ldg(a.seg + ws);   // {begin, end, first row, pieces}
-        int64_t p = sg.x;
-        const int64_t p1 = sg.y;
-        int32_t row = sg.z;
-        const GraphCtx c = graph_ctx<MULTI>(a, row);
-        if (!c.active) continue;
-        int64_t row_end = __ldg(a.row_ptr + row + 1);
-        float2 yi = load_pos(a.pos + row);
-        float2 yi0 = yi;
-        for (; p < p1; ++p) {
-            if (p >= row_end) {
-                write_oriented_source<RED>(a, row, yi, yi0, 1, flags);
-                do {
-                    ++row;
-                    row_end = __ldg(a.row_ptr + row + 1);
-                } while (row_end <= p);
-                yi = load_pos(a.pos + row);
-                yi0 = yi;
-            }
-            const int4 en = load_entry(a.ent + p);   // {j, index of (i, j), index of (j, i), -}
-            oriented_entry<RED, G>(a, c, row, en.x, en.y, en.z, yi);
-        }
-        write_oriented_source<RED>(a, row, yi, yi0, sg.w, flags);
+    const int64_t groups = (a.num_segs + 31) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // a multiple of 32
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (groups << 5); w += stride) {
+        const int64_t ws = slot_of(w, groups, a.perm_mul, a.perm_add);
+        if (ws < a.num_segs) oriented_chunk<RED, G, MULTI>(a, ws, flags);
     }
     if (flags) atomicOr(a.status, flags);
 }
 
 // Multi-handle epoch (continuous batching): one launch runs one epoch of
-// several independent layouts.  The segments of all jobs form one index
-// space; lane w takes segment perm(w), finds its job by binary search over
-// the jobs' segment prefixes, and processes it exactly as the single-graph
-// kernel would with that job's arrays, epoch, step and seed.
+// several independent layouts.  The slots of all jobs form one slot space;
+// lane w takes slot_of(w), finds its job by binary search over the jobs'
+// slot prefixes, and processes the chunk exactly as the single-graph kernel
+// would with that job's arrays, epoch, step and seed.
 template <bool RED, int G>
 __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) multi_epoch_kernel(const MultiArgs m) {
     uint32_t flags = 0;
+    const int64_t groups = (m.total_segs + 31) >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < m.total_segs; w += stride) {
-        const int64_t ws = (int64_t)(((uint64_t)m.perm_mul * (uint64_t)w + (uint64_t)m.perm_add) %
-                                     (uint64_t)m.total_segs);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (groups << 5); w += stride) {
+        const int64_t ws = slot_of(w, groups, m.perm_mul, m.perm_add);
+        if (ws >= m.total_segs) continue;
         int32_t lo = 0, hi = m.num_jobs - 1;   // last job with seg_prefix <= ws
         while (lo < hi) {
             const int32_t mid = (lo + hi + 1) / 2;
@@ -300,9 +330,11 @@ __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) multi_epoch_ker
         OrientedArgs a;
         a.row_ptr = jd.row_ptr;
         a.ent = jd.ent;
-        a.seg = jd.seg;
+        a.meta = jd.meta;
         a.pos = jd.pos;
         a.num_segs = jd.num_segs;
+        a.nnz = jd.nnz;
+        a.seg_len = jd.seg_len;
         a.n = jd.n;
         a.k = m.k;
         a.epoch = jd.epoch;
@@ -312,28 +344,7 @@ __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) multi_epoch_ker
         a.node_graph = nullptr;
         a.graphs = nullptr;
         a.inflight_share = m.inflight_share;
-        const GraphCtx c = graph_ctx<false>(a, 0);
-        const int4 sg = __ldg(a.seg + (ws - jd.seg_prefix));
-        int64_t p = sg.x;
-        const int64_t p1 = sg.y;
-        int32_t row = sg.z;
-        int64_t row_end = __ldg(a.row_ptr + row + 1);
-        float2 yi = load_pos(a.pos + row);
-        float2 yi0 = yi;
-        for (; p < p1; ++p) {
-            if (p >= row_end) {
-                write_oriented_source<RED>(a, row, yi, yi0, 1, flags);
-                do {
-                    ++row;
-                    row_end = __ldg(a.row_ptr + row + 1);
-                } while (row_end <= p);
-                yi = load_pos(a.pos + row);
-                yi0 = yi;
-            }
-            const int4 en = load_entry(a.ent + p);
-            oriented_entry<RED, G>(a, c, row, en.x, en.y, en.z, yi);
-        }
-        write_oriented_source<RED>(a, row, yi, yi0, sg.w, flags);
+        oriented_chunk<RED, G, false>(a, ws - jd.seg_prefix, flags);
     }
     if (flags) atomicOr(m.status, flags);
 }

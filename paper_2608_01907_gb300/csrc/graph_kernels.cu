@@ -144,6 +144,38 @@ __global__ void orient_rowptr_kernel(const int64_t *__restrict__ row_ptr, const 
         act_row_ptr[i] = pos[row_ptr[i]];
 }
 
+// Chunk layout of the oriented list (the stored order is described with
+// ChunkLayout).  One thread per entry p of the row-major list copies it from
+// its place under `from` to its place under `to`; the thread of a chunk's
+// first entry also writes the slot's {row, chunk}.
+__global__ void chunk_layout_kernel(const int4 *__restrict__ src, const ChunkLayout from, int4 *__restrict__ dst,
+                                    const ChunkLayout to, int2 *__restrict__ meta, const int64_t *__restrict__ act_rp,
+                                    int32_t n, int64_t nnz) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        int64_t q = p;
+        if (from.T > 0) {
+            const int64_t c = p / from.T;
+            q = chunk_entry_index(chunk_slot(from, c), from.S, from.T, p - c * from.T);
+        }
+        const int64_t c = p / to.T;
+        const int64_t t = p - c * to.T;
+        const int64_t slot = chunk_slot(to, c);
+        dst[chunk_entry_index(slot, to.S, to.T, t)] = src[q];
+        if (t == 0) {
+            int32_t lo = 0, hi = n - 1;   // last row starting at or before p: the row holding p
+            while (lo < hi) {
+                const int32_t mid = lo + (hi - lo + 1) / 2;
+                if (act_rp[mid] <= p)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            meta[slot] = make_int2(lo, (int32_t)c);
+        }
+    }
+}
+
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double warp_part[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -198,17 +230,19 @@ __global__ void objective_edges_kernel(const int64_t *__restrict__ row_ptr, cons
 
 // U^a over an oriented list (each undirected edge once), walking its segments.
 __global__ void objective_oriented_kernel(const int64_t *__restrict__ row_ptr, const int4 *__restrict__ ent,
-                                          const int4 *__restrict__ seg, int64_t num_segs,
+                                          const int2 *__restrict__ meta, const ChunkLayout L, int64_t nnz,
                                           const float2 *__restrict__ pos, double *partial) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double acc = 0.0;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < num_segs; w += stride) {
-        const int4 sg = seg[w];
-        int32_t row = sg.z;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < L.S; w += stride) {
+        const int2 mt = meta[w];   // {row of the first entry, chunk}
+        int32_t row = mt.x;
         int64_t row_end = row_ptr[row + 1];
         float2 yi = pos[row];
+        const int64_t p0 = (int64_t)mt.y * L.T;
+        const int64_t p1 = p0 + L.T < nnz ? p0 + L.T : nnz;
         float part = 0.0f;
-        for (int64_t p = sg.x; p < sg.y; ++p) {
+        for (int64_t p = p0; p < p1; ++p) {
             if (p >= row_end) {
                 do {
                     ++row;
@@ -216,7 +250,7 @@ __global__ void objective_oriented_kernel(const int64_t *__restrict__ row_ptr, c
                 } while (row_end <= p);
                 yi = pos[row];
             }
-            const float2 yj = pos[ent[p].x];
+            const float2 yj = pos[ent[chunk_entry_index(w, L.S, L.T, p - p0)].x];
             const float dx = yi.x - yj.x, dy = yi.y - yj.y;
             const float r2 = fmaf(dx, dx, dy * dy);
             part += kAlpha * (0.5f * r2 + 0.5f * kBeta * log1pf(r2));
@@ -385,9 +419,17 @@ cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int4 *seg, int64_t num_segs,
-                                      const float2 *pos, double *partial, int grid, cudaStream_t s) {
-    objective_oriented_kernel<<<grid, 256, 0, s>>>(row_ptr, ent, seg, num_segs, pos, partial);
+cudaError_t launch_chunk_layout(const int4 *src, const ChunkLayout &from, int4 *dst, const ChunkLayout &to,
+                                int2 *meta, const int64_t *act_rp, int32_t n, int64_t nnz, cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;
+    chunk_layout_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(src, from, dst, to, meta, act_rp, n, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int2 *meta,
+                                      const ChunkLayout &L, int64_t nnz, const float2 *pos, double *partial,
+                                      int grid, cudaStream_t s) {
+    objective_oriented_kernel<<<grid, 256, 0, s>>>(row_ptr, ent, meta, L, nnz, pos, partial);
     return cudaGetLastError();
 }
 

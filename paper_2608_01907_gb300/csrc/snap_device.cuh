@@ -78,8 +78,10 @@ __device__ __forceinline__ int4 load_cols4(const int32_t *p) {
     return __ldcs(reinterpret_cast<const int4 *>(p));
 }
 
-// One oriented entry {j, index of (i, j), index of (j, i), unused}, streamed.
-__device__ __forceinline__ int4 load_entry(const int4 *p) { return __ldcs(p); }
+// One oriented entry {j, index of (i, j), index of (j, i), row-major index}.
+// Read through L1: the 32 lanes of a warp walk one compact run of entries
+// over several iterations, so a line fetched for one lane serves others.
+__device__ __forceinline__ int4 load_entry(const int4 *p) { return __ldg(p); }
 
 // int64 fixed point (2^-32) of one force component, clamped to +-2^20.
 __device__ __forceinline__ long long to_fixed(float v, uint32_t &flags) {

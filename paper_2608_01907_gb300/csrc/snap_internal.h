@@ -67,19 +67,47 @@ struct SyncArgs {
     const GraphInfo *graphs;
 };
 
-// Oriented bundle list: entry p of row i is {j, CSR index of (i, j), CSR
-// index of (j, i), 0} for a partner j ranked below i; segments are
-// {begin, end, first row, pieces}: whole rows, or one of `pieces` pieces of a
-// long row.
+// Oriented bundle list: entry {j, CSR index of (i, j), CSR index of (j, i), 0}
+// for each partner j ranked below i, row-major (rows in vertex order).  The
+// list is cut into chunks of T consecutive entries (a chunk may cross row
+// boundaries; the last one may be short); chunk c goes to slot
+// (mul * c + add) mod S, S = ceil(nnz / T), so neighbouring slots hold
+// unrelated parts of the graph.  The slots of a slot group (32 slots; the
+// last group may have fewer, W) store their entries interleaved: entry t of
+// slot s is at (s / 32) * 32 * T + t * W + s % 32, so a warp on one slot
+// group reads W consecutive entries per step.  The array holds S * T entries.
+struct ChunkLayout {
+    int32_t T;     // entries per chunk
+    int64_t S;     // chunks (slots)
+    int64_t mul;   // slot of chunk c: (mul * c + add) mod S, gcd(mul, S) = 1
+    int64_t add;
+};
+
+__host__ __device__ inline int64_t chunk_slot(const ChunkLayout &L, int64_t c) {
+    return (int64_t)(((uint64_t)L.mul * (uint64_t)c + (uint64_t)L.add) % (uint64_t)L.S);
+}
+
+// Slots in the group of `slot` (32 except in the last group).
+__host__ __device__ inline int64_t chunk_group_width(int64_t slot, int64_t S) {
+    const int64_t rest = S - ((slot >> 5) << 5);
+    return rest < 32 ? rest : 32;
+}
+
+__host__ __device__ inline int64_t chunk_entry_index(int64_t slot, int64_t S, int32_t T, int64_t t) {
+    return (slot >> 5) * 32 * (int64_t)T + t * chunk_group_width(slot, S) + (slot & 31);
+}
+
 struct OrientedArgs {
-    const int64_t *row_ptr;   // n + 1 offsets into ent
-    const int4 *ent;          // one entry per undirected edge
-    const int4 *seg;          // num_segs segments
+    const int64_t *row_ptr;   // n + 1 row offsets of the oriented list (row-major positions)
+    const int4 *ent;          // entries in the stored (slot-interleaved) order
+    const int2 *meta;         // per slot: {row of the chunk's first entry, chunk id}
     float2 *pos;
-    int64_t num_segs;
-    int64_t perm_mul;         // segment order of this epoch: (perm_mul * w + perm_add) mod num_segs
-    int64_t perm_add;
+    int64_t num_segs;         // slots S
+    int64_t nnz;              // entries of the list
+    int32_t seg_len;          // entries per chunk T
     int32_t n;
+    int64_t perm_mul;         // order of the 32-slot groups this epoch: (perm_mul * g + perm_add) mod groups
+    int64_t perm_add;
     int32_t k;
     uint32_t epoch;           // single graph: the epoch; batch: the tick
     uint64_t seed;
@@ -87,7 +115,7 @@ struct OrientedArgs {
     uint32_t *status;
     const int32_t *node_graph;   // batch only: graph of every vertex
     const GraphInfo *graphs;     // batch only
-    float inflight_share;        // lanes in flight / segments (share of segments running at once)
+    float inflight_share;        // lanes in flight / slots (share of the chunks running at once)
 };
 
 cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s);
@@ -97,15 +125,16 @@ cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid,
 struct JobDesc {
     const int64_t *row_ptr;
     const int4 *ent;
-    const int4 *seg;
+    const int2 *meta;
     float2 *pos;
     int64_t num_segs;
-    int64_t seg_prefix;     // segments of the jobs before this one
+    int64_t seg_prefix;     // slots of the jobs before this one
+    int64_t nnz;
     uint64_t seed;
     int32_t n;
     uint32_t epoch;
     float eta;
-    int32_t pad[3];
+    int32_t seg_len;
 };
 
 struct MultiArgs {
@@ -113,7 +142,7 @@ struct MultiArgs {
     int32_t num_jobs;
     int32_t k;
     int64_t total_segs;
-    int64_t perm_mul;         // segment order: (perm_mul * w + perm_add) mod total_segs
+    int64_t perm_mul;         // order of the 32-slot groups, as OrientedArgs
     int64_t perm_add;
     uint32_t *status;
     float inflight_share;
@@ -147,12 +176,17 @@ cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx
                                   cudaStream_t s);
 cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,
                                  cudaStream_t s);
+// Moves the oriented entries from layout `from` (T == 0: plain row-major) to
+// layout `to` and writes `to`'s slot table.
+cudaError_t launch_chunk_layout(const int4 *src, const ChunkLayout &from, int4 *dst, const ChunkLayout &to,
+                                int2 *meta, const int64_t *act_rp, int32_t n, int64_t nnz, cudaStream_t s);
 // Objective partial sums (FP64), one per block, summed on the host in order.
 cudaError_t launch_objective_edges(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                    const float2 *pos, int64_t nnz, int32_t seg_len, double *partial, int grid,
                                    cudaStream_t s);
-cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int4 *seg, int64_t num_segs,
-                                      const float2 *pos, double *partial, int grid, cudaStream_t s);
+cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int2 *meta,
+                                      const ChunkLayout &L, int64_t nnz, const float2 *pos, double *partial,
+                                      int grid, cudaStream_t s);
 cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n,
                                          double *partial, int grid, cudaStream_t s);
 // Batch: sum over graphs of (1 / (2 (n_g - 1))) * sum over ordered pairs of the
