@@ -20,6 +20,14 @@ Parity status per function:
   sync                        pinned (S = 1 equals Y + eta * displacement;
                               chunk bounds by hand; cap by closed form)
   neighborhood_preservation   pinned (hand-computed 6-node case, lattice case)
+  alias_build                 pinned (hand-worked two-node table; the table's
+                              exact distribution equals q/Q within 2^-32 per
+                              column; equal weights give full columns)
+  edge_negatives (weighted)   pinned (chi^2 against P(s|i) including the
+                              16-rejection fallback; forced fallback word count)
+  weighted objective/gradient pinned (Monte-Carlo displacement mean -> -2 grad U
+                              with P(s|i); finite differences; uniform q equals
+                              the uniform objective)
 """
 from __future__ import annotations
 
@@ -68,19 +76,25 @@ def _load():
     lib.oracle_step_size.restype = f64
     lib.oracle_pair_terms.argtypes = [f64, f64, P]
     lib.oracle_pair_terms.restype = None
-    lib.oracle_seq.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, u64, i64, P, P]
+    lib.oracle_seq.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, u64, i64, P, P, P, P]
     lib.oracle_seq.restype = ctypes.c_int
     lib.oracle_sync_chunk_bounds.argtypes = [P, i32, i32, P]
     lib.oracle_sync_chunk_bounds.restype = None
-    lib.oracle_epoch_displacement.argtypes = [P, P, i32, P, i32, i32, u64, P]
+    lib.oracle_epoch_displacement.argtypes = [P, P, i32, P, i32, i32, u64, P, P, P]
     lib.oracle_epoch_displacement.restype = ctypes.c_int
-    lib.oracle_sync.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, f64]
+    lib.oracle_sync.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, f64, P, P]
     lib.oracle_sync.restype = ctypes.c_int
-    lib.oracle_objective.argtypes = [P, P, i32, P, i32, P]
+    lib.oracle_objective.argtypes = [P, P, i32, P, i32, P, P]
     lib.oracle_objective.restype = ctypes.c_int
-    lib.oracle_objective_sampled.argtypes = [P, P, i32, P, i32, i64, u64, P]
+    lib.oracle_objective_sampled.argtypes = [P, P, i32, P, i32, i64, u64, P, P]
     lib.oracle_objective_sampled.restype = ctypes.c_int
-    lib.oracle_exact_gradient.argtypes = [P, P, i32, P, i32, P]
+    lib.oracle_exact_gradient.argtypes = [P, P, i32, P, i32, P, P]
+    lib.oracle_quantize_weights.argtypes = [P, i32, P]
+    lib.oracle_quantize_weights.restype = ctypes.c_int
+    lib.oracle_alias_build.argtypes = [P, i32, P, P]
+    lib.oracle_alias_build.restype = ctypes.c_int
+    lib.oracle_edge_negatives.argtypes = [u64, u32, u64, i32, i32, i32, P, P, P]
+    lib.oracle_edge_negatives.restype = u32
     lib.oracle_exact_gradient.restype = ctypes.c_int
     lib.oracle_neighborhood_preservation.argtypes = [P, P, i32, P, P, i32]
     lib.oracle_neighborhood_preservation.restype = f64
@@ -140,12 +154,68 @@ def pair_terms(dx: float, dy: float) -> np.ndarray:
     return out
 
 
+class Sampler:
+    """Weighted negatives: integer weights q (uint64, n) and their alias table.
+
+    ``Sampler.degree(row_ptr)`` weighs a node by its degree;
+    ``Sampler.weights(w)`` quantises caller weights (float32 >= 0)."""
+
+    def __init__(self, q):
+        self.q = np.ascontiguousarray(q, dtype=np.uint64)
+        self.prob, self.alias = alias_build(self.q)
+
+    @classmethod
+    def degree(cls, row_ptr):
+        return cls(np.diff(np.asarray(row_ptr, dtype=np.int64)).astype(np.uint64))
+
+    @classmethod
+    def weights(cls, w):
+        return cls(quantize_weights(w))
+
+
+def _tables(sampler):
+    if sampler is None:
+        return None, None
+    return _p(sampler.prob), _p(sampler.alias)
+
+
+def _q(sampler):
+    return _p(sampler.q) if sampler is not None else None
+
+
+def quantize_weights(w) -> np.ndarray:
+    wf = np.ascontiguousarray(w, dtype=np.float32)
+    q = np.zeros(wf.size, dtype=np.uint64)
+    if _load().oracle_quantize_weights(_p(wf), wf.size, _p(q)) != 0:
+        raise ValueError("weights must be finite, >= 0 and not all zero")
+    return q
+
+
+def alias_build(q):
+    qa = np.ascontiguousarray(q, dtype=np.uint64)
+    prob = np.zeros(qa.size, dtype=np.uint32)
+    alias = np.zeros(qa.size, dtype=np.int32)
+    if _load().oracle_alias_build(_p(qa), qa.size, _p(prob), _p(alias)) != 0:
+        raise ValueError("alias table needs n >= 1 and a positive total weight")
+    return prob, alias
+
+
+def edge_negatives(e, t, seed, i, n, k, sampler=None):
+    """The k negatives of directed edge e (source i) in epoch t and the words used."""
+    out = np.zeros(max(k, 1), dtype=np.int32)
+    pr, al = _tables(sampler)
+    used = _load().oracle_edge_negatives(e, t, seed, i, n, k, pr, al, _p(out))
+    return out[:k], int(used)
+
+
 def seq(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, shuffle_seed=None,
-        epoch_begin=0, max_edges_per_epoch=-1, return_energy=False, shuffle=True, order=None):
+        epoch_begin=0, max_edges_per_epoch=-1, return_energy=False, shuffle=True, order=None,
+        sampler=None):
     """Algorithm 1 (sequential, immediate updates).  Returns the final (n,2) float64.
 
     shuffle=False visits the directed edges in CSR order; `order` (a
-    permutation of the CSR edge indices) fixes the visiting order."""
+    permutation of the CSR edge indices) fixes the visiting order; `sampler`
+    (a Sampler) draws weighted negatives instead of uniform ones."""
     rp, ci = _csr(row_ptr, col_idx)
     Y = _positions(Y0).copy()
     kind, eta0, eta_min, total = _sched(schedule)
@@ -158,7 +228,8 @@ def seq(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, shuffle_seed=
             raise ValueError("order must be a permutation of the CSR edge indices")
     rc = _load().oracle_seq(_p(rp), _p(ci), n, _p(Y), epoch_begin, epochs, k, kind, eta0, eta_min,
                             total, seed, int(bool(shuffle)), shuffle_seed, max_edges_per_epoch,
-                            _p(en) if return_energy else None, _p(od) if od is not None else None)
+                            _p(en) if return_energy else None, _p(od) if od is not None else None,
+                            *_tables(sampler))
     if rc != 0:
         raise MemoryError("oracle_seq failed to allocate")
     return (Y, en[:epochs]) if return_energy else Y
@@ -171,48 +242,48 @@ def sync_chunk_bounds(row_ptr, n, S) -> np.ndarray:
     return out
 
 
-def epoch_displacement(row_ptr, col_idx, n, Y, t, k, seed) -> np.ndarray:
+def epoch_displacement(row_ptr, col_idx, n, Y, t, k, seed, sampler=None) -> np.ndarray:
     rp, ci = _csr(row_ptr, col_idx)
     Yd = _positions(Y)
     D = np.zeros((n, 2))
-    _load().oracle_epoch_displacement(_p(rp), _p(ci), n, _p(Yd), t, k, seed, _p(D))
+    _load().oracle_epoch_displacement(_p(rp), _p(ci), n, _p(Yd), t, k, seed, *_tables(sampler), _p(D))
     return D
 
 
 def sync(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, substeps=1, cap=0.0,
-         epoch_begin=0):
+         epoch_begin=0, sampler=None):
     """Chunked synchronous (Jacobi) epochs.  Returns the final (n,2) float64."""
     rp, ci = _csr(row_ptr, col_idx)
     Y = _positions(Y0).copy()
     kind, eta0, eta_min, total = _sched(schedule)
     rc = _load().oracle_sync(_p(rp), _p(ci), n, _p(Y), epoch_begin, epochs, k, kind, eta0, eta_min,
-                             total, seed, substeps, cap)
+                             total, seed, substeps, cap, *_tables(sampler))
     if rc != 0:
         raise MemoryError("oracle_sync failed to allocate")
     return Y
 
 
-def objective(row_ptr, col_idx, n, Y, k) -> dict:
+def objective(row_ptr, col_idx, n, Y, k, sampler=None) -> dict:
     rp, ci = _csr(row_ptr, col_idx)
     Yd = _positions(Y)
     out = np.zeros(4)
-    _load().oracle_objective(_p(rp), _p(ci), n, _p(Yd), k, _p(out))
+    _load().oracle_objective(_p(rp), _p(ci), n, _p(Yd), k, _q(sampler), _p(out))
     return dict(attr=out[0], rep=out[1], total=out[2], rep_designed=out[3])
 
 
-def objective_sampled(row_ptr, col_idx, n, Y, k, pairs, seed) -> dict:
+def objective_sampled(row_ptr, col_idx, n, Y, k, pairs, seed, sampler=None) -> dict:
     rp, ci = _csr(row_ptr, col_idx)
     Yd = _positions(Y)
     out = np.zeros(4)
-    _load().oracle_objective_sampled(_p(rp), _p(ci), n, _p(Yd), k, pairs, seed, _p(out))
+    _load().oracle_objective_sampled(_p(rp), _p(ci), n, _p(Yd), k, pairs, seed, _q(sampler), _p(out))
     return dict(attr=out[0], rep=out[1], total=out[2])
 
 
-def exact_gradient(row_ptr, col_idx, n, Y, k) -> np.ndarray:
+def exact_gradient(row_ptr, col_idx, n, Y, k, sampler=None) -> np.ndarray:
     rp, ci = _csr(row_ptr, col_idx)
     Yd = _positions(Y)
     G = np.zeros((n, 2))
-    _load().oracle_exact_gradient(_p(rp), _p(ci), n, _p(Yd), k, _p(G))
+    _load().oracle_exact_gradient(_p(rp), _p(ci), n, _p(Yd), k, _q(sampler), _p(G))
     return G
 
 

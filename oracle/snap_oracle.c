@@ -20,6 +20,10 @@
  *     such mode; it is the deterministic reference for the library's
  *     synchronous mode.
  *   - Neighbourhood preservation NP with r = 2 (Section 4.1, Metrics).
+ *   - Weighted negatives (degree or caller weights, the future work of
+ *     Section 6) through an alias table, and the objective whose expected
+ *     gradient they follow (Section 3.3's derivation with P(s|i) in place of
+ *     1/(|V|-1)).
  *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As
  *     Easy as 1, 2, 3", SC'11) for the negative draws.
  *
@@ -44,8 +48,16 @@
  *   - Random words: word w of the stream of directed edge e in epoch t is
  *     component (w mod 4) of Philox4x32-10(counter = (e_lo, e_hi, t, w div 4),
  *     key = (seed_lo, seed_hi)); e is the edge's index in the row-major CSR.
- *     Negative m of edge e = (i, j) uses word m:  u = floor(word*(n-1)/2^32),
- *     s = u + (u >= i).
+ *     The negatives of edge e = (i, j) consume its words in order.  Uniform
+ *     (the paper's sampler) takes one word per negative:
+ *     u = floor(word*(n-1)/2^32), s = u + (u >= i).
+ *   - Weighted negatives (the paper's future work, Section 6: negatives drawn
+ *     in proportion to a node weight -- the degree, or a caller's weight):
+ *     Walker's alias method (Vose's construction) over integer weights q_s,
+ *     two words per attempt -- column c = floor(w0*n/2^32), s = c if
+ *     w1 < prob[c] else alias[c] -- an attempt that yields s = i is rejected
+ *     and the next two words are tried; after 16 rejections the uniform rule
+ *     above is applied to the next word.
  *
  * Build: plain C11, compiled with -ffp-contract=off so that no multiply-add
  * is fused (the rotation test relies on exact IEEE rounding of each op).
@@ -106,6 +118,176 @@ int32_t oracle_uniform_negative(uint32_t word, int32_t i, int32_t n)
 {
     uint32_t u = (uint32_t)(((uint64_t)word * (uint64_t)(uint32_t)(n - 1)) >> 32);
     return (int32_t)(u + (u >= (uint32_t)i ? 1u : 0u));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Weighted negative sampling (Section 6 names non-uniform negatives as      */
+/* future work; the weight is the degree for the DEGREE sampler).            */
+/* ------------------------------------------------------------------------ */
+
+/* Caller weights (float, >= 0, finite, not all zero) to integers:
+ * q_s = llround(w_s / max_w * 2^32), so 0 <= q_s <= 2^32.  Returns 0 or -1. */
+int oracle_quantize_weights(const float *w, int32_t n, uint64_t *q)
+{
+    double wmax = 0.0;
+    for (int32_t s = 0; s < n; ++s) {
+        double v = (double)w[s];
+        if (!(v >= 0.0) || isinf(v))
+            return -1;
+        if (v > wmax)
+            wmax = v;
+    }
+    if (!(wmax > 0.0))
+        return -1;
+    for (int32_t s = 0; s < n; ++s)
+        q[s] = (uint64_t)llround((double)w[s] / wmax * 4294967296.0);
+    return 0;
+}
+
+/* floor(a * 2^32 / b) for a < b < 2^63, by binary long division. */
+static uint32_t frac32(uint64_t a, uint64_t b)
+{
+    uint32_t r = 0;
+    for (int bit = 0; bit < 32; ++bit) {
+        a <<= 1;
+        r <<= 1;
+        if (a >= b) {
+            a -= b;
+            r |= 1u;
+        }
+    }
+    return r;
+}
+
+/* Alias table of the integer weights q (Walker; Vose's construction in exact
+ * integer arithmetic).  In units where every column holds Q = sum q, node s
+ * brings n*q_s.  Worklists: `small` (n*q_s < Q) is a first-in-first-out
+ * queue and `large` a stack, both filled in increasing s.  Repeatedly the
+ * first small node l keeps its own mass in column l and the top large node
+ * g fills the rest of column l (alias[l] = g) and loses that much; g moves
+ * to the small queue when it falls below Q.  Nodes left over fill their own
+ * column.  prob[c] = floor(mass_c * 2^32 / Q) for a column shared with its
+ * alias; a full column has prob 0xFFFFFFFF and alias c.
+ * Requires n * max q < 2^64 and 0 < Q < 2^63.  Returns 0 or -1. */
+int oracle_alias_build(const uint64_t *q, int32_t n, uint32_t *prob, int32_t *alias)
+{
+    uint64_t Q = 0;
+    for (int32_t s = 0; s < n; ++s)
+        Q += q[s];
+    if (n < 1 || Q == 0)
+        return -1;
+    uint64_t *mass = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int32_t *small = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *large = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!mass || !small || !large) {
+        free(mass);
+        free(small);
+        free(large);
+        return -1;
+    }
+    int64_t s_head = 0, s_tail = 0, l_top = 0;
+    for (int32_t s = 0; s < n; ++s) {
+        mass[s] = (uint64_t)n * q[s];
+        if (mass[s] < Q)
+            small[s_tail++] = s;
+        else
+            large[l_top++] = s;
+    }
+    for (int32_t s = 0; s < n; ++s) {
+        prob[s] = 0xFFFFFFFFu;
+        alias[s] = s;
+    }
+    while (s_head < s_tail && l_top > 0) {
+        int32_t l = small[s_head++];
+        int32_t g = large[l_top - 1];
+        prob[l] = frac32(mass[l], Q);
+        alias[l] = g;
+        mass[g] -= Q - mass[l];
+        if (mass[g] < Q) {
+            --l_top;
+            small[s_tail++] = g;
+        }
+    }
+    /* exact arithmetic conserves n*Q in total: whatever is left is full */
+    free(mass);
+    free(small);
+    free(large);
+    return 0;
+}
+
+/* Word stream of one directed edge: the negatives consume it in order. */
+typedef struct {
+    uint64_t e;
+    uint32_t t;
+    uint64_t seed;
+    uint32_t next;
+} word_cursor;
+
+static uint32_t take_word(word_cursor *c)
+{
+    return oracle_edge_word(c->e, c->t, c->next++, c->seed);
+}
+
+/* The next negative of source i (uniform when prob == NULL). */
+static int32_t draw_negative(word_cursor *c, int32_t i, int32_t n, const uint32_t *prob, const int32_t *alias)
+{
+    if (prob) {
+        for (int attempt = 0; attempt < 16; ++attempt) {
+            uint32_t w0 = take_word(c);
+            uint32_t w1 = take_word(c);
+            int32_t col = (int32_t)(((uint64_t)w0 * (uint64_t)(uint32_t)n) >> 32);
+            int32_t s = w1 < prob[col] ? col : alias[col];
+            if (s != i)
+                return s;
+        }
+    }
+    return oracle_uniform_negative(take_word(c), i, n);
+}
+
+/* Negatives m = 0..k-1 of directed edge e in epoch t, and the number of
+ * words they consumed (for the tests). */
+uint32_t oracle_edge_negatives(uint64_t e, uint32_t t, uint64_t seed, int32_t i, int32_t n, int32_t k,
+                               const uint32_t *prob, const int32_t *alias, int32_t *out)
+{
+    word_cursor c = {e, t, seed, 0u};
+    for (int32_t m = 0; m < k; ++m)
+        out[m] = draw_negative(&c, i, n, prob, alias);
+    return c.next;
+}
+
+/* Probability that one negative of source i is s (s != i) under the sampler
+ * with weights q (NULL: uniform, 1/(n-1)).  A weighted attempt accepts with
+ * probability 1 - rho_i, rho_i = q_i/Q; after 16 rejections the draw is
+ * uniform: P(s|i) = (1 - rho_i^16) q_s / (Q - q_i) + rho_i^16 / (n-1).
+ * (The alias table realises q_s/Q up to its 2^-32 thresholds.) */
+static double negative_prob(const uint64_t *q, uint64_t Q, int32_t n, int32_t i, int32_t s)
+{
+    if (!q)
+        return 1.0 / (double)(n - 1);
+    double rho = (double)q[i] / (double)Q;
+    double r2 = rho * rho, r4 = r2 * r2, r8 = r4 * r4, r16 = r8 * r8;
+    uint64_t rest = Q - q[i];
+    double p = rest > 0 ? (1.0 - r16) * (double)q[s] / (double)rest : 0.0;
+    return p + r16 / (double)(n - 1);
+}
+
+/* Pair coefficient of the objective generalised from Section 3.3:
+ * c_ij = d_i P(j|i) + d_j P(i|j); w_ij = c_ij / 2.  Uniform: (d_i+d_j)/(n-1). */
+static double pair_coefficient(const int64_t *row_ptr, const uint64_t *q, uint64_t Q, int32_t n, int32_t i,
+                               int32_t j)
+{
+    double di = (double)(row_ptr[i + 1] - row_ptr[i]);
+    double dj = (double)(row_ptr[j + 1] - row_ptr[j]);
+    return di * negative_prob(q, Q, n, i, j) + dj * negative_prob(q, Q, n, j, i);
+}
+
+static uint64_t weight_total(const uint64_t *q, int32_t n)
+{
+    uint64_t Q = 0;
+    if (q)
+        for (int32_t s = 0; s < n; ++s)
+            Q += q[s];
+    return Q;
 }
 
 /* Step size of epoch t (paper: "decaying over epochs", updated once per epoch). */
@@ -197,7 +379,7 @@ int oracle_seq(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double
                int32_t epoch_begin, int32_t epochs, int32_t k,
                int32_t sched_kind, double eta0, double eta_min, int32_t total_epochs,
                uint64_t seed, int32_t shuffle, uint64_t shuffle_seed, int64_t max_edges_per_epoch,
-               double *actual_energy, const int64_t *given_order)
+               double *actual_energy, const int64_t *given_order, const uint32_t *prob, const int32_t *alias)
 {
     int64_t nnz = row_ptr[n];
     int32_t *src = row_of_edges(row_ptr, n);
@@ -245,9 +427,9 @@ int oracle_seq(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double
             yi[1] += eta * fy;
             yj[0] -= eta * fx;
             yj[1] -= eta * fy;
+            word_cursor cur = {(uint64_t)e, (uint32_t)t, seed, 0u};
             for (int32_t m = 0; m < k; ++m) {
-                uint32_t word = oracle_edge_word((uint64_t)e, (uint32_t)t, (uint32_t)m, seed);
-                int32_t s = oracle_uniform_negative(word, i, n);
+                int32_t s = draw_negative(&cur, i, n, prob, alias);
                 double *ys = Y + 2 * (int64_t)s;
                 double sx = yi[0] - ys[0], sy = yi[1] - ys[1];
                 if (actual_energy)
@@ -287,7 +469,7 @@ void oracle_sync_chunk_bounds(const int64_t *row_ptr, int32_t n, int32_t S, int3
  * added into D (n x 2). */
 static void chunk_displacement(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
                                const double *Y, int32_t r0, int32_t r1, int32_t k,
-                               uint32_t t, uint64_t seed, double *D)
+                               uint32_t t, uint64_t seed, const uint32_t *prob, const int32_t *alias, double *D)
 {
     for (int32_t i = r0; i < r1; ++i) {
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
@@ -299,9 +481,9 @@ static void chunk_displacement(const int64_t *row_ptr, const int32_t *col_idx, i
             D[2 * (int64_t)i + 1] += fy;
             D[2 * (int64_t)j] -= fx;
             D[2 * (int64_t)j + 1] -= fy;
+            word_cursor cur = {(uint64_t)e, t, seed, 0u};
             for (int32_t m = 0; m < k; ++m) {
-                int32_t s = oracle_uniform_negative(
-                    oracle_edge_word((uint64_t)e, t, (uint32_t)m, seed), i, n);
+                int32_t s = draw_negative(&cur, i, n, prob, alias);
                 repulsion_on_i(Y[2 * (int64_t)i] - Y[2 * (int64_t)s],
                                Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)s + 1], &fx, &fy);
                 D[2 * (int64_t)i] += fx;
@@ -316,10 +498,11 @@ static void chunk_displacement(const int64_t *row_ptr, const int32_t *col_idx, i
 /* One frozen-position epoch displacement (all rows, one chunk): the sampled
  * estimate whose expectation Section 3.3 derives. */
 int oracle_epoch_displacement(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
-                              const double *Y, int32_t t, int32_t k, uint64_t seed, double *D)
+                              const double *Y, int32_t t, int32_t k, uint64_t seed,
+                              const uint32_t *prob, const int32_t *alias, double *D)
 {
     memset(D, 0, sizeof(double) * 2 * (size_t)n);
-    chunk_displacement(row_ptr, col_idx, n, Y, 0, n, k, (uint32_t)t, seed, D);
+    chunk_displacement(row_ptr, col_idx, n, Y, 0, n, k, (uint32_t)t, seed, prob, alias, D);
     return 0;
 }
 
@@ -330,7 +513,7 @@ int oracle_epoch_displacement(const int64_t *row_ptr, const int32_t *col_idx, in
 int oracle_sync(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double *Y,
                 int32_t epoch_begin, int32_t epochs, int32_t k,
                 int32_t sched_kind, double eta0, double eta_min, int32_t total_epochs,
-                uint64_t seed, int32_t S, double cap)
+                uint64_t seed, int32_t S, double cap, const uint32_t *prob, const int32_t *alias)
 {
     if (S < 1)
         S = 1;
@@ -347,7 +530,8 @@ int oracle_sync(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, doubl
         double eta = oracle_step_size(sched_kind, eta0, eta_min, total_epochs, t);
         for (int32_t c = 0; c < S; ++c) {
             memset(D, 0, sizeof(double) * 2 * (size_t)n);
-            chunk_displacement(row_ptr, col_idx, n, Y, bound[c], bound[c + 1], k, (uint32_t)t, seed, D);
+            chunk_displacement(row_ptr, col_idx, n, Y, bound[c], bound[c + 1], k, (uint32_t)t, seed, prob, alias,
+                               D);
             double limit = cap * eta / eta0;
             for (int32_t i = 0; i < n; ++i) {
                 double sx = eta * D[2 * (int64_t)i], sy = eta * D[2 * (int64_t)i + 1];
@@ -370,11 +554,13 @@ int oracle_sync(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, doubl
 
 /* ------------------------------------------------------------------------ */
 /* Objective (Eq. 4) with the weight realised by uniform edge-centric       */
-/* sampling (Section 3.3): w_ij = (d_i+d_j) / (2(n-1)).                     */
-/* out = {attraction, repulsion, total, repulsion with Eq. 5's 2n weight}.  */
+/* sampling (Section 3.3): w_ij = (d_i+d_j) / (2(n-1)); with weighted       */
+/* negatives (q != NULL) w_ij = c_ij / 2 from pair_coefficient.             */
+/* out = {attraction, repulsion, total, repulsion with Eq. 5's 2n weight    */
+/* (uniform only; 0 otherwise)}.                                            */
 /* ------------------------------------------------------------------------ */
 int oracle_objective(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
-                     const double *Y, int32_t k, double out[4])
+                     const double *Y, int32_t k, const uint64_t *q, double out[4])
 {
     double attr = 0.0;
     for (int32_t i = 0; i < n; ++i)
@@ -384,6 +570,19 @@ int oracle_objective(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
                 attr += energy_attr(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
                                     Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
         }
+    if (q) {
+        uint64_t Q = weight_total(q, n);
+        double rep = 0.0;   /* sum over i<j of w_ij U^r */
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t j = i + 1; j < n; ++j)
+                rep += 0.5 * pair_coefficient(row_ptr, q, Q, n, i, j) *
+                       energy_rep(Y[2 * (int64_t)i] - Y[2 * (int64_t)j], Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
+        out[0] = attr;
+        out[1] = (double)k * rep;
+        out[2] = attr + out[1];
+        out[3] = 0.0;
+        return 0;
+    }
     double rep_num = 0.0;   /* sum over i<j of (d_i + d_j) U^r */
     for (int32_t i = 0; i < n; ++i) {
         double di = (double)(row_ptr[i + 1] - row_ptr[i]);
@@ -407,8 +606,9 @@ int oracle_objective(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
  * key = seed).  out as in oracle_objective (out[3] left 0). */
 int oracle_objective_sampled(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
                              const double *Y, int32_t k, int64_t pairs, uint64_t seed,
-                             double out[4])
+                             const uint64_t *q, double out[4])
 {
+    uint64_t Q = weight_total(q, n);
     double attr = 0.0;
     for (int32_t i = 0; i < n; ++i)
         for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
@@ -427,11 +627,12 @@ int oracle_objective_sampled(const int64_t *row_ptr, const int32_t *col_idx, int
         int32_t j = oracle_uniform_negative(w[1], i, n);
         double di = (double)(row_ptr[i + 1] - row_ptr[i]);
         double dj = (double)(row_ptr[j + 1] - row_ptr[j]);
-        acc += (di + dj) * energy_rep(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
-                                      Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
+        double c = q ? pair_coefficient(row_ptr, q, Q, n, i, j) : (di + dj) / (double)(n - 1);
+        acc += c * energy_rep(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
+                              Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1]);
     }
     double npairs = 0.5 * (double)n * (double)(n - 1);
-    double rep = pairs > 0 && n > 1 ? (double)k * (acc / (double)pairs) * npairs / (2.0 * (double)(n - 1)) : 0.0;
+    double rep = pairs > 0 && n > 1 ? (double)k * (acc / (double)pairs) * npairs / 2.0 : 0.0;
     out[0] = attr;
     out[1] = rep;
     out[2] = attr + rep;
@@ -441,7 +642,7 @@ int oracle_objective_sampled(const int64_t *row_ptr, const int32_t *col_idx, int
 
 /* Gradient of the objective above with respect to every y_i (n x 2). */
 int oracle_exact_gradient(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
-                          const double *Y, int32_t k, double *G)
+                          const double *Y, int32_t k, const uint64_t *q, double *G)
 {
     memset(G, 0, sizeof(double) * 2 * (size_t)n);
     for (int32_t i = 0; i < n; ++i)
@@ -456,17 +657,20 @@ int oracle_exact_gradient(const int64_t *row_ptr, const int32_t *col_idx, int32_
     if (n < 2)
         return 0;
     double norm = (double)k / (2.0 * (double)(n - 1));
+    uint64_t Q = weight_total(q, n);
     for (int32_t i = 0; i < n; ++i) {
         double di = (double)(row_ptr[i + 1] - row_ptr[i]);
         for (int32_t j = 0; j < n; ++j) {
             if (j == i)
                 continue;
             double dj = (double)(row_ptr[j + 1] - row_ptr[j]);
+            /* k * w_ij, w_ij = c_ij / 2 */
+            double kw = q ? 0.5 * (double)k * pair_coefficient(row_ptr, q, Q, n, i, j) : norm * (di + dj);
             double fx, fy;
             repulsion_on_i(Y[2 * (int64_t)i] - Y[2 * (int64_t)j],
                            Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)j + 1], &fx, &fy);
-            G[2 * (int64_t)i] -= norm * (di + dj) * fx;
-            G[2 * (int64_t)i + 1] -= norm * (di + dj) * fy;
+            G[2 * (int64_t)i] -= kw * fx;
+            G[2 * (int64_t)i + 1] -= kw * fy;
         }
     }
     return 0;
