@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--impl", default="snap", choices=["snap", "reference"])
     p.add_argument("--k", type=int, default=3)
     p.add_argument("--mode", default="hogwild", choices=["hogwild", "hogwild_red", "sync"])
+    p.add_argument("--sampler", default="uniform", choices=["uniform", "degree"],
+                   help="negatives: uniform (the paper's) or degree-weighted (alias table)")
     p.add_argument("--scale", type=int, default=22)
     p.add_argument("--edges", type=int, default=34_000_000)
     p.add_argument("--seed", type=int, default=1)
@@ -90,7 +92,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("epoch_kernels.cu", "snap_device.cuh", "snap_internal.h"):
+    for f in ("epoch_device.cuh", "epoch_kernels.cu", "snap_device.cuh", "snap_internal.h"):
         with open(os.path.join(ROOT, "paper_2608_01907_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -162,17 +164,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(n, row_ptr, col_idx, Y0, k, sample_edges, seed):
+def oracle_sampler(name, row_ptr):
+    import oracle
+    return oracle.Sampler.degree(row_ptr) if name == "degree" else None
+
+
+def cpu_baseline(n, row_ptr, col_idx, Y0, k, sample_edges, seed, sampler="uniform"):
     """The FP64 oracle (Algorithm 1, one host core) on a bounded sample: one
     epoch limited to the first `sample_edges` directed edges of its shuffled
     order.  The one-off shuffle is timed separately and not charged."""
     import oracle
     sched = dict(kind=0, eta0=1.0, eta_min=1e-3, total_epochs=EPOCHS)
+    sam = oracle_sampler(sampler, row_ptr)
     t0 = time.perf_counter()
     oracle.seq(row_ptr, col_idx, n, Y0, 0, k, sched, seed=seed)
     t_shuffle = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.seq(row_ptr, col_idx, n, Y0, 1, k, sched, seed=seed, max_edges_per_epoch=sample_edges)
+    oracle.seq(row_ptr, col_idx, n, Y0, 1, k, sched, seed=seed, max_edges_per_epoch=sample_edges, sampler=sam)
     t_run = time.perf_counter() - t0
     work = max(t_run - t_shuffle, 1e-9)
     upd = sample_edges * (1 + k)
@@ -205,6 +213,7 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     sched = dict(kind=0, eta0=1.0, eta_min=1e-3, total_epochs=EPOCHS)
+    sam = oracle_sampler(args.sampler, row_ptr)
     M = args.cpu_sample_edges
     t0 = time.perf_counter()
     oracle.seq(row_ptr, col_idx, n, Y0, 0, args.k, sched, seed=args.seed)
@@ -212,7 +221,7 @@ def run_reference(args, rank, world):
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.seq(row_ptr, col_idx, n, Y0, 1, args.k, sched, seed=args.seed, max_edges_per_epoch=M)
+        oracle.seq(row_ptr, col_idx, n, Y0, 1, args.k, sched, seed=args.seed, max_edges_per_epoch=M, sampler=sam)
         dt = time.perf_counter() - t0 - t_shuffle
         if s >= args.warmup:
             times.append(max(dt, 1e-9))
@@ -224,7 +233,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "s_per_layout_extrapolated": per_layout,
             "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{args.k}-{EPOCHS}ep-bfs", "n": n,
-                       "undirected_edges": args.edges, "k": args.k, "epochs": EPOCHS},
+                       "undirected_edges": args.edges, "k": args.k, "epochs": EPOCHS, "sampler": args.sampler},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: 1 epoch limited to {M} directed edges, FP64 Algorithm 1, "
                                        f"1 thread; shuffle ({t_shuffle:.2f} s, once per layout) excluded"},
@@ -247,8 +256,9 @@ def run_snap(args, rank, world, local_rank):
     mode = {"hogwild": snap.MODE_HOGWILD, "hogwild_red": snap.MODE_HOGWILD_RED, "sync": snap.MODE_SYNC}[args.mode]
     # the synchronous mode needs its step cap on hub-heavy graphs: a hub's
     # frozen-position step sums ~10^5 pulls
+    sampler = snap.SAMPLER_DEGREE if args.sampler == "degree" else snap.SAMPLER_UNIFORM
     opts = snap.make_options(mode=mode, sync_substeps=16 if mode == snap.MODE_SYNC else 1,
-                             sync_cap=1.0 if mode == snap.MODE_SYNC else 0.0)
+                             sync_cap=1.0 if mode == snap.MODE_SYNC else 0.0, sampler=sampler)
     sched = snap.linear_schedule(eta0=1.0, total_epochs=EPOCHS)
     seed = args.seed + rank
     Y0 = initial_positions(n, args.seed)
@@ -307,10 +317,14 @@ def run_snap(args, rank, world, local_rank):
     snap.snap_layout_destroy(h)
     if rank == 0 and not args.no_extras:
         # the other modes on the same graph, 5 epochs each (not the headline)
-        for mname, mcode in (("hogwild_red", snap.MODE_HOGWILD_RED), ("sync", snap.MODE_SYNC)):
-            if mcode == mode:
-                continue
-            o2 = snap.make_options(mode=mcode, sync_substeps=16, sync_cap=1.0)
+        variants = [(f"mode_{m}", c, sampler) for m, c in (("hogwild", snap.MODE_HOGWILD),
+                                                             ("hogwild_red", snap.MODE_HOGWILD_RED),
+                                                             ("sync", snap.MODE_SYNC)) if c != mode]
+        other = snap.SAMPLER_UNIFORM if sampler == snap.SAMPLER_DEGREE else snap.SAMPLER_DEGREE
+        variants += [(f"sampler_{'uniform' if other == snap.SAMPLER_UNIFORM else 'degree'}_{m}", c, other)
+                     for m, c in (("hogwild", snap.MODE_HOGWILD), ("hogwild_red", snap.MODE_HOGWILD_RED))]
+        for mname, mcode, msampler in variants:
+            o2 = snap.make_options(mode=mcode, sync_substeps=16, sync_cap=1.0, sampler=msampler)
             h2 = snap.snap_layout_create(row_ptr, col_idx, None, n, o2, stream)
             Y.copy_(Y0_d)
             snap.snap_layout_epochs(h2, Y, 0, 1, k, sched, seed, stream)
@@ -320,8 +334,8 @@ def run_snap(args, rank, world, local_rank):
             e1.record(stream)
             snap.snap_layout_check(h2, stream)
             ms = e0.elapsed_time(e1) / 5
-            extras[f"mode_{mname}"] = {"ms_per_epoch": ms, "updates_per_s": nnz * (1 + k) / (ms / 1e3),
-                                       "options": "S=16, cap=1.0" if mcode == snap.MODE_SYNC else "default"}
+            extras[mname] = {"ms_per_epoch": ms, "updates_per_s": nnz * (1 + k) / (ms / 1e3),
+                             "options": "S=16, cap=1.0" if mcode == snap.MODE_SYNC else "default"}
             snap.snap_layout_destroy(h2)
 
     # ceiling of the access pattern that binds the epoch kernel: random
@@ -384,7 +398,8 @@ def run_snap(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n, row_ptr, col_idx, Y0.astype(np.float64), k, args.cpu_sample_edges, args.seed)
+        cpu = cpu_baseline(n, row_ptr, col_idx, Y0.astype(np.float64), k, args.cpu_sample_edges, args.seed,
+                           args.sampler)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -393,7 +408,7 @@ def run_snap(args, rank, world, local_rank):
                 "data": "synthetic",
                 "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{k}-{EPOCHS}ep-bfs", "n": n,
                            "undirected_edges": args.edges, "directed_edges": nnz, "k": k, "epochs": EPOCHS,
-                           "mode": args.mode, "isolated_nodes": int(n - nonempty),
+                           "mode": args.mode, "sampler": args.sampler, "isolated_nodes": int(n - nonempty),
                            "l2": "inputs larger than L2: the 272 MB edge stream is re-read every epoch; the "
                                  "33.5 MB positions stay L2-resident by design",
                            "parallelism": f"replicas x{world}"},

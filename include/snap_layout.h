@@ -75,8 +75,14 @@ typedef enum {
     SNAP_MODE_SYNC = 2
 } snap_mode;
 
-/* Negative-sample distribution.  Only UNIFORM (the paper's, Algorithm 1) is
- * implemented; the others return SNAP_ERR_NOT_SUPPORTED. */
+/* Negative-sample distribution.  UNIFORM is the paper's (Algorithm 1: s
+ * uniform over V \ {i}; the degree weighting of Eq. 4 then arises implicitly,
+ * Section 3.3).  DEGREE and WEIGHTS draw s in proportion to its degree or to
+ * a caller weight -- the non-uniform negatives the paper leaves to future
+ * work (Section 6) -- through an alias table (snap_sampler_table): two
+ * random words per attempt, an attempt yielding s = i rejected, the uniform
+ * rule after 16 rejections.  The objective then uses the pair weight
+ * w_ij = (d_i P(j|i) + d_j P(i|j)) / 2 with the sampler's P(s|i). */
 typedef enum {
     SNAP_SAMPLER_UNIFORM = 0,
     SNAP_SAMPLER_DEGREE = 1,
@@ -99,7 +105,7 @@ typedef struct {
 typedef struct {
     int32_t mode;             /* snap_mode */
     int32_t sampler;          /* snap_sampler */
-    const float *node_weights;/* host, n; SNAP_SAMPLER_WEIGHTS only (unused now) */
+    const float *node_weights;/* host, n floats >= 0 (read during create only); SNAP_SAMPLER_WEIGHTS */
     int32_t sync_substeps;    /* S >= 1 row chunks per epoch in SNAP_MODE_SYNC */
     float sync_cap;           /* > 0: clip each node's sync step to cap*eta_t/eta0 */
     int32_t segment_edges;    /* work per lane segment, a multiple of 4 in [4, 4096]: in the HOGWILD
@@ -195,6 +201,23 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
                                void *cuda_stream);
 
 /*
+ * snap_layout_epochs_energy -- snap_layout_epochs that also reports the
+ * "actual energy" of every epoch (Section 3.3, compared there with the
+ * effective energy of Eq. 4 evaluated after each epoch): half the sum, over
+ * the directed steps of the epoch, of U^a of the step's pair and U^r of each
+ * drawn pair, each evaluated on the positions the update used (frozen
+ * positions in SNAP_MODE_SYNC).  Summed in FP64 per block from FP32 terms.
+ *
+ *   actual_energy  device, epochs doubles, 8-byte aligned; overwritten
+ *                  asynchronously on the stream (entry e = epoch epoch_begin + e).
+ * The call is never captured into a CUDA graph.  Other arguments, ordering
+ * and errors as snap_layout_epochs; NOT_SUPPORTED for a batch handle.
+ */
+snap_status snap_layout_epochs_energy(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
+                                      int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                                      double *actual_energy, void *cuda_stream);
+
+/*
  * snap_layout_objective -- the energy the method descends (Eq. 4 with the
  * weight realised by uniform sampling, Section 3.3):
  *   U = sum_{(i,j) in E, i<j} U^a(r_ij) + k * sum_{i<j} w_ij U^r(r_ij),
@@ -245,6 +268,27 @@ snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int3
  * stream of its latest call).  The handle's memory is allocated
  * stream-ordered on the stream given to create. */
 void snap_layout_destroy(snap_layout_t h);
+
+/*
+ * snap_sampler_table -- the alias table of a weighted sampler for one graph
+ * (host only; snap_layout_create builds the same table, per graph of a
+ * batch).  Integer weights q: the degrees (DEGREE) or
+ * llround(w / max w * 2^32) (WEIGHTS).  Vose's construction in exact integer
+ * arithmetic: the small vertices (n q_s < sum q) are served first-in
+ * first-out in increasing id, the large ones from a stack filled in
+ * increasing id; a column shared with alias a keeps its vertex with
+ * probability threshold / 2^32 (threshold = floor(kept * 2^32 / sum q)), a
+ * full column has threshold 0xFFFFFFFF and itself as alias.
+ *
+ *   sampler    SNAP_SAMPLER_DEGREE or SNAP_SAMPLER_WEIGHTS.
+ *   row_ptr    host, n + 1 (DEGREE; unused for WEIGHTS).
+ *   node_weights  host, n floats >= 0 (WEIGHTS; unused for DEGREE).
+ *   threshold, alias  host outputs, n each (alias: vertex ids).
+ * Errors: INVALID_ARG (unknown sampler, NULL array, a negative, NaN or
+ * infinite weight, all weights zero).
+ */
+snap_status snap_sampler_table(int32_t sampler, const int64_t *row_ptr, const float *node_weights, int32_t n,
+                               uint32_t *threshold, int32_t *alias);
 
 /*
  * snap_graph_reorder -- locality relabelling of a symmetric CSR (host only).

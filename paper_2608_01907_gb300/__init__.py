@@ -22,7 +22,8 @@ __all__ = [
     "snap_options_default", "snap_layout_create", "snap_layout_epochs", "snap_layout_objective",
     "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
     "snap_layout_run", "snap_last_error", "Layout", "linear_schedule", "snap_sync_epochs_noalloc",
-    "snap_layout_create_batch", "batch_union", "snap_layout_autotune", "MultiEpoch",
+    "snap_layout_create_batch", "batch_union", "snap_layout_autotune", "MultiEpoch", "snap_sampler_table",
+    "snap_layout_epochs_energy",
 ]
 
 MODE_HOGWILD, MODE_HOGWILD_RED, MODE_SYNC = 0, 1, 2
@@ -88,6 +89,8 @@ def load_library():
     lib.snap_layout_create_batch.restype = st
     lib.snap_layout_epochs.argtypes = [P, P, i32, i32, i32, P, u64, P]
     lib.snap_layout_epochs.restype = st
+    lib.snap_layout_epochs_energy.argtypes = [P, P, i32, i32, i32, P, u64, P, P]
+    lib.snap_layout_epochs_energy.restype = st
     lib.snap_layout_objective.argtypes = [P, P, i32, i32, i64, u64, P, P, P, P]
     lib.snap_layout_objective.restype = st
     lib.snap_layout_check.argtypes = [P, P]
@@ -98,6 +101,8 @@ def load_library():
     lib.snap_layout_device_bytes.restype = i64
     lib.snap_layout_destroy.argtypes = [P]
     lib.snap_layout_destroy.restype = None
+    lib.snap_sampler_table.argtypes = [i32, P, P, i32, P, P]
+    lib.snap_sampler_table.restype = st
     lib.snap_graph_reorder.argtypes = [P, P, i32, P, P, P]
     lib.snap_graph_reorder.restype = st
     lib.snap_layout_run.argtypes = [P, P, i32, P, P, i32, i32, P, u64, P]
@@ -165,12 +170,18 @@ def snap_options_default() -> SnapOptions:
 
 def make_options(mode: int = MODE_HOGWILD, sync_substeps: int = 1, sync_cap: float = 0.0,
                  segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM,
-                 cuda_graph: bool = False, max_inflight: float = 0.0) -> SnapOptions:
+                 cuda_graph: bool = False, max_inflight: float = 0.0, node_weights=None) -> SnapOptions:
+    """Options for snap_layout_create; node_weights (n floats) goes with SAMPLER_WEIGHTS
+    and is kept alive by the returned object."""
     o = snap_options_default()
     o.mode, o.sync_substeps, o.sync_cap = mode, sync_substeps, sync_cap
     o.segment_edges, o.block_threads, o.sampler = segment_edges, block_threads, sampler
     o.flags = FLAG_CUDA_GRAPH if cuda_graph else 0
     o.max_inflight = max_inflight
+    if node_weights is not None:
+        w = _host(node_weights, np.float32)
+        o.node_weights = w.ctypes.data
+        o._node_weights = w
     return o
 
 
@@ -206,6 +217,18 @@ def snap_layout_epochs(h, positions, epoch_begin: int, epochs: int, neg_samples:
                                              ctypes.byref(schedule), seed, _stream(stream)))
 
 
+def snap_layout_epochs_energy(h, positions, epoch_begin: int, epochs: int, neg_samples: int,
+                              schedule: SnapSchedule, seed: int, energy, stream=None) -> None:
+    """As snap_layout_epochs, also writing each epoch's actual energy into
+    `energy` (a CUDA float64 tensor of `epochs` elements)."""
+    if not (energy.is_cuda and energy.dtype.is_floating_point and energy.element_size() == 8
+            and energy.is_contiguous() and energy.numel() >= epochs):
+        raise ValueError("energy must be a contiguous CUDA float64 tensor with `epochs` elements")
+    _check(load_library().snap_layout_epochs_energy(h, _device_positions(positions), epoch_begin, epochs,
+                                                    neg_samples, ctypes.byref(schedule), seed,
+                                                    ctypes.c_void_p(energy.data_ptr()), _stream(stream)))
+
+
 def snap_layout_objective(h, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0,
                           seed: int = 0, stream=None) -> tuple[float, float, float]:
     a, r, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
@@ -234,6 +257,18 @@ def snap_layout_device_bytes(h) -> int:
 
 def snap_layout_destroy(h) -> None:
     load_library().snap_layout_destroy(h)
+
+
+def snap_sampler_table(sampler: int, row_ptr=None, node_weights=None, n: int | None = None):
+    """(threshold uint32[n], alias int32[n]) of a weighted sampler (see the C header)."""
+    rp = None if row_ptr is None else _host(row_ptr, np.int64)
+    w = None if node_weights is None else _host(node_weights, np.float32)
+    if n is None:
+        n = rp.size - 1 if rp is not None else w.size
+    thr = np.zeros(n, np.uint32)
+    al = np.zeros(n, np.int32)
+    _check(load_library().snap_sampler_table(sampler, _ptr(rp), _ptr(w), n, _ptr(thr), _ptr(al)))
+    return thr, al
 
 
 def snap_graph_reorder(row_ptr, col_idx, n: int | None = None):
@@ -374,6 +409,12 @@ class Layout:
                seed: int) -> None:
         _device_positions(positions, self.n)
         snap_layout_epochs(self.handle, positions, epoch_begin, epochs, neg_samples, schedule, seed, self.stream)
+
+    def epochs_energy(self, positions, epoch_begin: int, epochs: int, neg_samples: int, schedule: SnapSchedule,
+                      seed: int, energy) -> None:
+        _device_positions(positions, self.n)
+        snap_layout_epochs_energy(self.handle, positions, epoch_begin, epochs, neg_samples, schedule, seed, energy,
+                                  self.stream)
 
     def objective(self, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0, seed: int = 0):
         _device_positions(positions, self.n)

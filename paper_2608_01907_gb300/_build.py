@@ -17,8 +17,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsnap_layout.so")
 PROBE_LIB = os.path.join(HERE, "libsnap_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "epoch_kernels.cu", "graph_kernels.cu", "sync_noalloc.cu"]
-CPP_SOURCES = ["reorder.cpp"]
+CU_SOURCES = ["capi.cu", "epoch_kernels.cu", "epoch_weighted.cu", "epoch_energy.cu", "graph_kernels.cu",
+              "sync_noalloc.cu"]
+CPP_SOURCES = ["reorder.cpp", "sampler.cpp"]
 
 
 def _nvcc() -> str:

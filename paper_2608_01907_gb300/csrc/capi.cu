@@ -14,6 +14,7 @@
 
 #include "../../include/snap_layout.h"
 #include "snap_internal.h"
+#include "snap_sampler.h"
 
 using namespace snap;
 
@@ -187,6 +188,10 @@ struct snap_layout {
     bool graphs_set = false;
     snap_schedule graphs_sched{};
     uint64_t graphs_seed = 0;
+    // weighted negatives (SNAP_SAMPLER_DEGREE / _WEIGHTS): per-vertex alias
+    // table {threshold, graph-local alias} and objective factors
+    uint2 *d_alias = nullptr;
+    float4 *d_objw = nullptr;
     uint32_t *d_status = nullptr;   // [0] fault bits, [1] validation bits
     double *d_partial = nullptr;    // 2 * kObjGrid
     uint32_t *h_status = nullptr;   // pinned mirror of d_status[0]
@@ -195,6 +200,7 @@ struct snap_layout {
     int sms = 1;
     int grid_sync = 0, grid_apply = 0;
     int grid_oriented[2][5] = {{0}};   // [red][min(k, 4)], filled on first use
+    int grid_energy[2][5] = {{0}};     // the same for epochs that sum the actual energy
     std::vector<int64_t> chunk_edges;   // S + 1 edge offsets of the sync chunks
     int64_t device_bytes = 0;
     // CUDA graphs of captured epoch sequences (SNAP_FLAG_CUDA_GRAPH)
@@ -235,6 +241,10 @@ struct snap_layout {
         free_async(d_act_row_ptr);
         free_async(d_act_ent);
         free_async(d_act_meta);
+        free_async(d_alias);
+        free_async(d_objw);
+        d_alias = nullptr;
+        d_objw = nullptr;
         free_async(d_node_graph);
         free_async(d_graphs);
         d_node_graph = nullptr;
@@ -441,8 +451,10 @@ static snap_status check_csr_host(const int64_t *row_ptr, const int32_t *col_idx
 static snap_status check_options(const snap_options &o) {
     if (o.mode < SNAP_MODE_HOGWILD || o.mode > SNAP_MODE_SYNC)
         return fail(SNAP_ERR_INVALID_ARG, "unknown mode %d", o.mode);
-    if (o.sampler != SNAP_SAMPLER_UNIFORM)
-        return fail(SNAP_ERR_NOT_SUPPORTED, "sampler %d is not implemented (only SNAP_SAMPLER_UNIFORM)", o.sampler);
+    if (o.sampler < SNAP_SAMPLER_UNIFORM || o.sampler > SNAP_SAMPLER_WEIGHTS)
+        return fail(SNAP_ERR_INVALID_ARG, "unknown sampler %d", o.sampler);
+    if (o.sampler == SNAP_SAMPLER_WEIGHTS && !o.node_weights)
+        return fail(SNAP_ERR_INVALID_ARG, "SNAP_SAMPLER_WEIGHTS needs node_weights");
     if (o.sync_substeps < 1 || o.sync_substeps > (1 << 20))
         return fail(SNAP_ERR_INVALID_ARG, "sync_substeps = %d out of range [1, 2^20]", o.sync_substeps);
     if (!(o.sync_cap >= 0.0f) || !std::isfinite(o.sync_cap))
@@ -456,6 +468,38 @@ static snap_status check_options(const snap_options &o) {
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 256 || o.block_threads % 32 != 0))
         return fail(SNAP_ERR_INVALID_ARG, "block_threads = %d must be 0 or a multiple of 32 in [32, 256]",
                     o.block_threads);
+    return SNAP_OK;
+}
+
+// Alias tables and objective factors of a weighted sampler, one per graph of
+// the handle (graph-local ids), built on the host in exact integer arithmetic.
+static snap_status sampler_tables(const snap_options &o, const int64_t *row_ptr, int32_t n,
+                                  const int32_t *graph_offsets, int32_t num_graphs, std::vector<uint2> &table,
+                                  std::vector<float4> &objw) {
+    table.assign((size_t)n, make_uint2(0xFFFFFFFFu, 0u));
+    objw.assign((size_t)n, make_float4(0.f, 0.f, 0.f, 0.f));
+    std::vector<uint64_t> q;
+    std::vector<uint32_t> thr;
+    std::vector<int32_t> al;
+    const int32_t graphs = graph_offsets ? num_graphs : 1;
+    for (int32_t g = 0; g < graphs; ++g) {
+        const int32_t v0 = graph_offsets ? graph_offsets[g] : 0;
+        const int32_t v1 = graph_offsets ? graph_offsets[g + 1] : n;
+        const int32_t ng = v1 - v0;
+        q.assign((size_t)ng, 0);
+        const int rc = sampler_weights(o.sampler, row_ptr, o.node_weights, v0, v1, q.data());
+        if (rc == 1) return fail(SNAP_ERR_INVALID_ARG, "node_weights must be finite and >= 0");
+        if (rc == 2) {
+            if (row_ptr[v1] > row_ptr[v0])
+                return fail(SNAP_ERR_INVALID_ARG, "the sampler's weights of graph %d are all zero", g);
+            for (uint64_t &x : q) x = 1;   // no edges: the table is never used
+        }
+        thr.assign((size_t)ng, 0);
+        al.assign((size_t)ng, 0);
+        alias_table(q.data(), ng, thr.data(), al.data());
+        for (int32_t s = 0; s < ng; ++s) table[(size_t)(v0 + s)] = make_uint2(thr[(size_t)s], (uint32_t)al[(size_t)s]);
+        sampler_objective_factors(row_ptr, q.data(), v0, v1, objw.data() + v0);
+    }
     return SNAP_OK;
 }
 
@@ -478,6 +522,12 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     if (opts) o = *opts;
     st = check_options(o);
     if (st != SNAP_OK) return st;
+    std::vector<uint2> alias_host;
+    std::vector<float4> objw_host;
+    if (o.sampler != SNAP_SAMPLER_UNIFORM) {
+        st = sampler_tables(o, row_ptr, n, graph_offsets, num_graphs, alias_host, objw_host);
+        if (st != SNAP_OK) return st;
+    }
 
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     snap_layout *h = new (std::nothrow) snap_layout();
@@ -524,6 +574,10 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     SNAP_ALLOC(h->d_status, sizeof(uint32_t) * 4);
     SNAP_ALLOC(h->d_partial, sizeof(double) * 2 * kObjGrid);
     if (disp_bytes) SNAP_ALLOC(h->d_disp, disp_bytes);
+    if (!alias_host.empty()) {
+        SNAP_ALLOC(h->d_alias, sizeof(uint2) * (size_t)n);
+        SNAP_ALLOC(h->d_objw, sizeof(float4) * (size_t)n);
+    }
     if (h->num_graphs > 1) {
         SNAP_ALLOC(h->d_node_graph, sizeof(int32_t) * (size_t)n);
         SNAP_ALLOC(h->d_graphs, sizeof(GraphInfo) * (size_t)h->num_graphs);
@@ -573,6 +627,12 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
                                   cudaMemcpyHostToDevice, stream), "copy graph table");
     }
     if (h->d_disp) SNAP_CUDA(cudaMemsetAsync(h->d_disp, 0, disp_bytes, stream), "clear displacement");
+    if (h->d_alias) {
+        SNAP_CUDA(cudaMemcpyAsync(h->d_alias, alias_host.data(), sizeof(uint2) * (size_t)n, cudaMemcpyHostToDevice,
+                                  stream), "copy alias table");
+        SNAP_CUDA(cudaMemcpyAsync(h->d_objw, objw_host.data(), sizeof(float4) * (size_t)n, cudaMemcpyHostToDevice,
+                                  stream), "copy objective factors");
+    }
     SNAP_CUDA(launch_segment_rows(h->d_row_ptr, n, h->nnz, h->seg_len, h->d_seg_row, h->num_segs, stream),
               "segment table kernel");
     SNAP_CUDA(launch_validate_csr(h->d_row_ptr, h->d_col, h->d_seg_row, n, h->nnz, h->seg_len, h->d_status + 1,
@@ -625,6 +685,21 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
         h->chunk_edges[(size_t)S] = h->nnz;
     }
     *out = h;
+    return SNAP_OK;
+}
+
+snap_status snap_sampler_table(int32_t sampler, const int64_t *row_ptr, const float *node_weights, int32_t n,
+                               uint32_t *threshold, int32_t *alias) {
+    if (sampler != SNAP_SAMPLER_DEGREE && sampler != SNAP_SAMPLER_WEIGHTS)
+        return fail(SNAP_ERR_INVALID_ARG, "sampler %d has no table", sampler);
+    if (n < 1 || !threshold || !alias) return fail(SNAP_ERR_INVALID_ARG, "NULL output or n < 1");
+    if (sampler == SNAP_SAMPLER_DEGREE ? !row_ptr : !node_weights)
+        return fail(SNAP_ERR_INVALID_ARG, "the sampler's input array is NULL");
+    std::vector<uint64_t> q((size_t)n);
+    const int rc = sampler_weights(sampler, row_ptr, node_weights, 0, n, q.data());
+    if (rc == 1) return fail(SNAP_ERR_INVALID_ARG, "node_weights must be finite and >= 0");
+    if (rc == 2) return fail(SNAP_ERR_INVALID_ARG, "all weights are zero");
+    alias_table(q.data(), n, threshold, alias);
     return SNAP_OK;
 }
 
@@ -682,7 +757,7 @@ static int inflight_grid(const snap_layout *h, int gmax) {
 // Enqueues the launches of epochs [epoch_begin, epoch_begin + epochs) on `stream`.
 static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_begin, int32_t epochs,
                                   int32_t neg_samples, const snap_schedule &sched, uint64_t seed,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, double *energy = nullptr) {
     const snap_schedule *schedule = &sched;
     cudaError_t err = cudaSuccess;
     for (int32_t ep = 0; ep < epochs; ++ep) {
@@ -710,6 +785,8 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
                     a.status = h->d_status;
                     a.node_graph = h->d_node_graph;
                     a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
+                    a.alias = h->d_alias;
+                    a.energy = energy ? energy + ep : nullptr;
                     const int64_t segs = (ee + h->seg_len - 1) / h->seg_len - eb / h->seg_len;
                     const int64_t want = (segs + h->block - 1) / h->block;
                     const int grid = (int)(want < h->grid_sync ? want : h->grid_sync);
@@ -740,9 +817,11 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
             a.status = h->d_status;
             a.node_graph = h->d_node_graph;
             a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
+            a.alias = h->d_alias;
+            a.energy = energy ? energy + ep : nullptr;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
             const int g = neg_samples < 4 ? neg_samples : 4;
-            const int gmax = h->grid_oriented[red][g];
+            const int gmax = energy ? h->grid_energy[red][g] : h->grid_oriented[red][g];
             if (h->act_num_segs == 0) continue;
             const int grid = inflight_grid(h, gmax);
             {
@@ -758,8 +837,8 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
     return cudaSuccess;
 }
 
-snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
-                               int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+static snap_status epochs_impl(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
+                               int32_t neg_samples, const snap_schedule *schedule, uint64_t seed, double *energy,
                                void *cuda_stream) {
     if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
     if (!positions) return fail(SNAP_ERR_INVALID_ARG, "positions is NULL");
@@ -771,6 +850,10 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
     if (st != SNAP_OK) return st;
     st = poll_status(h);
     if (st != SNAP_OK) return st;
+    if (energy && epochs > 0) {
+        const cudaError_t e = cudaMemsetAsync(energy, 0, sizeof(double) * (size_t)epochs, (cudaStream_t)cuda_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "clear actual energy");
+    }
     if (h->nnz == 0 || epochs == 0) return SNAP_OK;
 
     cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -802,9 +885,12 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
         const int g = neg_samples < 4 ? neg_samples : 4;
         if (h->grid_oriented[red][g] == 0)
             h->grid_oriented[red][g] =
-                h->sms * oriented_blocks_per_sm(red, neg_samples, h->block, h->num_graphs > 1);
+                h->sms * oriented_blocks_per_sm(red, neg_samples, h->block, h->num_graphs > 1, h->d_alias != nullptr);
+        if (energy && h->grid_energy[red][g] == 0)
+            h->grid_energy[red][g] =
+                h->sms * oriented_energy_blocks_per_sm(red, neg_samples, h->block, h->d_alias != nullptr);
     }
-    if ((h->opts.flags & SNAP_FLAG_CUDA_GRAPH) && epochs > 1) {
+    if ((h->opts.flags & SNAP_FLAG_CUDA_GRAPH) && epochs > 1 && !energy) {
         cudaGraphExec_t exec = nullptr;
         for (const CapturedEpochs &c : h->captured)
             if (c.pos == positions && c.epoch_begin == epoch_begin && c.epochs == epochs && c.k == neg_samples &&
@@ -839,7 +925,7 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
         err = cudaGraphLaunch(exec, stream);
         if (err != cudaSuccess) return cuda_fail(err, "epoch graph launch");
     } else {
-        err = enqueue_epochs(h, pos, epoch_begin, epochs, neg_samples, *schedule, seed, stream);
+        err = enqueue_epochs(h, pos, epoch_begin, epochs, neg_samples, *schedule, seed, stream, energy);
         if (err != cudaSuccess) return cuda_fail(err, "epoch launch");
     }
     if (!h->status_pending) {
@@ -850,6 +936,22 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
     }
     h->mark_use(stream);
     return SNAP_OK;
+}
+
+snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
+                               int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                               void *cuda_stream) {
+    return epochs_impl(h, positions, epoch_begin, epochs, neg_samples, schedule, seed, nullptr, cuda_stream);
+}
+
+snap_status snap_layout_epochs_energy(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
+                                      int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                                      double *actual_energy, void *cuda_stream) {
+    if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
+    if (!actual_energy || ((uintptr_t)actual_energy & 7u) != 0)
+        return fail(SNAP_ERR_INVALID_ARG, "actual_energy must be a non-NULL 8-byte aligned device buffer");
+    if (h->num_graphs > 1) return fail(SNAP_ERR_NOT_SUPPORTED, "the actual energy is reported for single graphs");
+    return epochs_impl(h, positions, epoch_begin, epochs, neg_samples, schedule, seed, actual_energy, cuda_stream);
 }
 
 snap_status snap_layout_check(snap_layout_t h, void *cuda_stream) {
@@ -895,13 +997,14 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
         return fail(SNAP_ERR_NOT_SUPPORTED, "the sampled objective is not available for a batch (use exact = 1)");
     if (err == cudaSuccess && h->n > 1) {
         if (h->num_graphs > 1)
-            err = launch_objective_pairs_batch(pos, h->d_deg, h->d_node_graph, h->d_graphs, h->n,
+            err = launch_objective_pairs_batch(pos, h->d_deg, h->d_objw, h->d_node_graph, h->d_graphs, h->n,
                                                h->d_partial + kObjGrid, kObjGrid, stream);
         else if (exact)
-            err = launch_objective_pairs_exact(pos, h->d_deg, h->n, h->d_partial + kObjGrid, kObjGrid, stream);
+            err = launch_objective_pairs_exact(pos, h->d_deg, h->d_objw, h->n, h->d_partial + kObjGrid, kObjGrid,
+                                               stream);
         else
-            err = launch_objective_pairs_sampled(pos, h->d_deg, h->n, pair_samples, seed, h->d_partial + kObjGrid,
-                                                 kObjGrid, stream);
+            err = launch_objective_pairs_sampled(pos, h->d_deg, h->d_objw, h->n, pair_samples, seed,
+                                                 h->d_partial + kObjGrid, kObjGrid, stream);
     }
     std::vector<double> part(2 * (size_t)kObjGrid);
     if (err == cudaSuccess)
@@ -918,9 +1021,9 @@ snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32
         rep = (double)neg_samples * 0.5 * pairsum;   // per-graph weights applied on the device
     } else if (h->n > 1) {
         const double n = (double)h->n;
-        // unordered-pair sum of (d_i + d_j) U^r
+        // unordered-pair sum of coef_ij U^r; w_ij = coef / (2 (n-1)) (uniform) or c_ij / 2 (weighted)
         const double unordered = exact ? 0.5 * pairsum : pairsum / (double)pair_samples * 0.5 * n * (n - 1.0);
-        rep = (double)neg_samples * unordered / (2.0 * (n - 1.0));
+        rep = (double)neg_samples * unordered * (h->d_objw ? 0.5 : 1.0 / (2.0 * (n - 1.0)));
     }
     if (out_attr) *out_attr = attr;
     if (out_rep) *out_rep = rep;
@@ -963,7 +1066,8 @@ snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int3
             if ((err = set_segments(h, ac, target, stream)) != cudaSuccess) break;
             h->block = block;
             h->grid_oriented[red][g] = 0;
-            h->grid_oriented[red][g] = h->sms * oriented_blocks_per_sm(red, neg_samples, block, h->num_graphs > 1);
+            h->grid_oriented[red][g] =
+                h->sms * oriented_blocks_per_sm(red, neg_samples, block, h->num_graphs > 1, h->d_alias != nullptr);
             err = enqueue_epochs(h, reinterpret_cast<float2 *>(scratch_positions), 0, 1, neg_samples, sched, 1,
                                  stream);
             if (err == cudaSuccess) err = cudaEventRecord(e0, stream);
@@ -1064,7 +1168,7 @@ struct snap_multi {
     cudaEvent_t copied = nullptr;
     bool copy_pending = false;
     int sms = 1;
-    int grid[2][5] = {{0}};
+    int grid[2][2][5] = {{{0}}};   // [red][weighted][min(k, 4)], filled on first use
     uint64_t calls = 0;
 
     void release() {
@@ -1151,6 +1255,7 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
         jd.num_segs = h->act_num_segs;
         jd.nnz = h->act_nnz;
         jd.seg_len = h->act_seg_len;
+        jd.alias = h->d_alias;
         jd.seg_prefix = total;
         jd.seed = seeds[q];
         jd.n = h->n;
@@ -1176,18 +1281,21 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
     a.perm_add = (int64_t)(mixkey % (uint64_t)groups);
     a.status = m->d_status;
     const int g = neg_samples < 4 ? neg_samples : 4;
-    if (m->grid[red][g] == 0) m->grid[red][g] = m->sms * multi_blocks_per_sm(red, neg_samples, 256);
+    int weighted = 0;
+    for (int32_t q = 0; q < used; ++q) weighted |= m->h_jobs[q].alias != nullptr;
+    if (m->grid[red][weighted][g] == 0)
+        m->grid[red][weighted][g] = m->sms * multi_blocks_per_sm(red, weighted, neg_samples, 256);
     // at most 1% of the jobs' entries in flight (as inflight_grid does for one handle)
     int64_t entries = 0;
     for (int32_t q = 0; q < count; ++q) entries += handles[q]->act_nnz;
     const int64_t want = (total + 255) / 256;
     int64_t gcap = ((int64_t)(0.01 * (double)entries) + 255) / 256;
-    int64_t gl = want < m->grid[red][g] ? want : m->grid[red][g];
+    int64_t gl = want < m->grid[red][weighted][g] ? want : m->grid[red][weighted][g];
     if (gcap < gl) gl = gcap;
     const int grid = (int)(gl > 0 ? gl : 1);
     a.inflight_share = (float)(((double)grid * 256.0 < (double)total ? (double)grid * 256.0 : (double)total) /
                                (double)total);
-    err = launch_multi_epoch(a, red, grid > 0 ? grid : 1, 256, stream);
+    err = launch_multi_epoch(a, red, weighted, grid > 0 ? grid : 1, 256, stream);
     if (err != cudaSuccess) return cuda_fail(err, "multi-handle epoch launch");
     for (int32_t q = 0; q < count; ++q) handles[q]->mark_use(stream);
     return SNAP_OK;

@@ -265,22 +265,34 @@ __global__ void objective_oriented_kernel(const int64_t *__restrict__ row_ptr, c
 // The host halves it (unordered pairs) and applies k / (2 (n-1)).
 constexpr int kPairTile = 256;
 
+// Pair coefficient of the objective: uniform negatives (d_i + d_j); weighted
+// negatives c_ij = d_i P(j|i) + d_j P(i|j) = x_i z_j + y_i + x_j z_i + y_j from
+// the per-vertex factors {x, y, z} (Section 3.3's derivation with P(s|i)).
+__device__ __forceinline__ float pair_coef(float di, float dj, const float4 &wi, const float4 &wj, bool weighted) {
+    return weighted ? fmaf(wi.x, wj.z, wi.y) + fmaf(wj.x, wi.z, wj.y) : di + dj;
+}
+
+template <bool WT>
 __global__ void __launch_bounds__(kPairTile) objective_pairs_exact_kernel(const float2 *__restrict__ pos,
                                                                           const int32_t *__restrict__ deg,
+                                                                          const float4 *__restrict__ wt,
                                                                           int32_t n, double *partial) {
     __shared__ float2 tp[kPairTile];
     __shared__ float td[kPairTile];
+    __shared__ float4 tw[WT ? kPairTile : 1];
     double acc = 0.0;
     for (int64_t base = (int64_t)blockIdx.x * kPairTile; base < n; base += (int64_t)gridDim.x * kPairTile) {
         const int64_t i = base + threadIdx.x;
         const bool valid = i < n;
         const float2 yi = valid ? pos[i] : make_float2(0.f, 0.f);
         const float di = valid ? (float)deg[i] : 0.f;
+        const float4 wi = (WT && valid) ? wt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int64_t jb = 0; jb < n; jb += kPairTile) {
             __syncthreads();
             const int64_t jl = jb + threadIdx.x;
             tp[threadIdx.x] = jl < n ? pos[jl] : make_float2(0.f, 0.f);
             td[threadIdx.x] = jl < n ? (float)deg[jl] : 0.f;
+            if (WT) tw[threadIdx.x] = jl < n ? wt[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
             if (valid) {
                 const int cnt = (int)min((int64_t)kPairTile, n - jb);
@@ -289,7 +301,8 @@ __global__ void __launch_bounds__(kPairTile) objective_pairs_exact_kernel(const 
                     const float dx = yi.x - tp[q].x, dy = yi.y - tp[q].y;
                     const float r2 = fmaf(dx, dx, dy * dy);
                     const float u = 0.5f * __frcp_rn(1.0f + r2);
-                    part += (jb + q == i) ? 0.0f : (di + td[q]) * u;
+                    const float c = pair_coef(di, td[q], wi, tw[WT ? q : 0], WT);
+                    part += (jb + q == i) ? 0.0f : c * u;
                 }
                 acc += (double)part;
             }
@@ -299,18 +312,21 @@ __global__ void __launch_bounds__(kPairTile) objective_pairs_exact_kernel(const 
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// Batch: per vertex i, (1 / (2 (n_g - 1))) * sum over j != i of its graph of
-// (d_i + d_j) U^r(r_ij); one thread per vertex, the graph's vertices in turn.
+// Batch: per vertex i, the sum over j != i of its graph of w_ij U^r(r_ij),
+// w_ij = (d_i + d_j) / (2 (n_g - 1)) for uniform negatives or c_ij / 2 for
+// weighted ones; one thread per vertex, the graph's vertices in turn.
 __global__ void objective_pairs_batch_kernel(const float2 *__restrict__ pos, const int32_t *__restrict__ deg,
-                                             const int32_t *__restrict__ node_graph,
+                                             const float4 *__restrict__ wt, const int32_t *__restrict__ node_graph,
                                              const GraphInfo *__restrict__ graphs, int32_t n, double *partial) {
     double acc = 0.0;
+    const bool weighted = wt != nullptr;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const GraphInfo gi = graphs[node_graph[i]];
         if (gi.n < 2) continue;
         const float2 yi = pos[i];
         const float di = (float)deg[i];
+        const float4 wi = weighted ? wt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         double sum = 0.0;
         float part = 0.0f;
         int cnt = 0;
@@ -319,7 +335,8 @@ __global__ void objective_pairs_batch_kernel(const float2 *__restrict__ pos, con
             const float2 yj = pos[j];
             const float dx = yi.x - yj.x, dy = yi.y - yj.y;
             const float r2 = fmaf(dx, dx, dy * dy);
-            part += (di + (float)deg[j]) * (0.5f * __frcp_rn(1.0f + r2));
+            const float4 wj = weighted ? wt[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            part += pair_coef(di, (float)deg[j], wi, wj, weighted) * (0.5f * __frcp_rn(1.0f + r2));
             if (++cnt == 256) {
                 sum += (double)part;
                 part = 0.0f;
@@ -327,17 +344,19 @@ __global__ void objective_pairs_batch_kernel(const float2 *__restrict__ pos, con
             }
         }
         sum += (double)part;
-        acc += sum / (2.0 * (double)(gi.n - 1));
+        acc += weighted ? 0.5 * sum : sum / (2.0 * (double)(gi.n - 1));
     }
     const double t = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 // Sampled unordered pairs: p -> Philox(ctr = (p_lo, p_hi, 0xFFFFFFFD, 0), key = seed);
-// i = floor(w0 n / 2^32), j = negative(w1) of i.  Returns sum of (d_i + d_j) U^r.
+// i = floor(w0 n / 2^32), j = negative(w1) of i.  Returns the sum of coef * U^r.
 __global__ void objective_pairs_sampled_kernel(const float2 *__restrict__ pos, const int32_t *__restrict__ deg,
-                                               int32_t n, int64_t pairs, uint64_t seed, double *partial) {
+                                               const float4 *__restrict__ wt, int32_t n, int64_t pairs,
+                                               uint64_t seed, double *partial) {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const bool weighted = wt != nullptr;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double acc = 0.0;
     float part = 0.0f;
@@ -349,7 +368,9 @@ __global__ void objective_pairs_sampled_kernel(const float2 *__restrict__ pos, c
         const float2 yi = pos[i], yj = pos[j];
         const float dx = yi.x - yj.x, dy = yi.y - yj.y;
         const float r2 = fmaf(dx, dx, dy * dy);
-        part += ((float)deg[i] + (float)deg[j]) * (0.5f * __frcp_rn(1.0f + r2));
+        const float4 wi = weighted ? wt[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 wj = weighted ? wt[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        part += pair_coef((float)deg[i], (float)deg[j], wi, wj, weighted) * (0.5f * __frcp_rn(1.0f + r2));
         if (++cnt == 256) {
             acc += (double)part;
             part = 0.0f;
@@ -439,22 +460,26 @@ cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n, double *partial,
-                                         int grid, cudaStream_t s) {
-    objective_pairs_exact_kernel<<<grid, kPairTile, 0, s>>>(pos, deg, n, partial);
+cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, const float4 *wt, int32_t n,
+                                         double *partial, int grid, cudaStream_t s) {
+    if (wt)
+        objective_pairs_exact_kernel<true><<<grid, kPairTile, 0, s>>>(pos, deg, wt, n, partial);
+    else
+        objective_pairs_exact_kernel<false><<<grid, kPairTile, 0, s>>>(pos, deg, nullptr, n, partial);
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const int32_t *node_graph,
-                                         const GraphInfo *graphs, int32_t n, double *partial, int grid,
-                                         cudaStream_t s) {
-    objective_pairs_batch_kernel<<<grid, 256, 0, s>>>(pos, deg, node_graph, graphs, n, partial);
+cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const float4 *wt,
+                                         const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
+                                         double *partial, int grid, cudaStream_t s) {
+    objective_pairs_batch_kernel<<<grid, 256, 0, s>>>(pos, deg, wt, node_graph, graphs, n, partial);
     return cudaGetLastError();
 }
 
-cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, int32_t n, int64_t pairs,
-                                           uint64_t seed, double *partial, int grid, cudaStream_t s) {
-    objective_pairs_sampled_kernel<<<grid, 256, 0, s>>>(pos, deg, n, pairs, seed, partial);
+cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, const float4 *wt, int32_t n,
+                                           int64_t pairs, uint64_t seed, double *partial, int grid,
+                                           cudaStream_t s) {
+    objective_pairs_sampled_kernel<<<grid, 256, 0, s>>>(pos, deg, wt, n, pairs, seed, partial);
     return cudaGetLastError();
 }
 

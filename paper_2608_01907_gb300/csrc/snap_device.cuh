@@ -40,6 +40,53 @@ __device__ __forceinline__ int32_t negative_of(uint32_t w, int32_t i, uint32_t n
     return (int32_t)(u + (u >= (uint32_t)i ? 1u : 0u));
 }
 
+// The word stream of one directed edge, consumed in order by its negatives
+// (word w is component w mod 4 of the Philox block w div 4).
+struct WordCursor {
+    int64_t e;       // edge index (graph-local)
+    uint32_t next;   // next word
+    uint32_t blk;    // Philox block held in buf (~0u: none)
+    uint4 buf;
+};
+
+__device__ __forceinline__ WordCursor word_cursor(int64_t e) {
+    WordCursor c;
+    c.e = e;
+    c.next = 0;
+    c.blk = ~0u;
+    c.buf = make_uint4(0, 0, 0, 0);
+    return c;
+}
+
+__device__ __forceinline__ uint32_t take_word(WordCursor &c, uint32_t t, uint2 key) {
+    const uint32_t b = c.next >> 2;
+    if (b != c.blk) {
+        c.buf = edge_words(c.e, t, b, key);
+        c.blk = b;
+    }
+    const uint32_t q = c.next & 3u;
+    ++c.next;
+    return q == 0 ? c.buf.x : q == 1 ? c.buf.y : q == 2 ? c.buf.z : c.buf.w;
+}
+
+// Weighted negative (degree or caller weights) through an alias table of n
+// entries {threshold, alias} (graph-local ids): two words per attempt --
+// column floor(w0 n / 2^32), kept when w1 < threshold, else its alias; an
+// attempt that yields the source is rejected, and after 16 rejections the
+// uniform rule takes the next word.  Returns a graph-local id.
+__device__ __forceinline__ int32_t weighted_negative(WordCursor &c, uint32_t t, uint2 key, const uint2 *table,
+                                                     uint32_t n, int32_t src) {
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        const uint32_t w0 = take_word(c, t, key);
+        const uint32_t w1 = take_word(c, t, key);
+        const uint32_t col = __umulhi(w0, n);
+        const uint2 en = __ldg(table + col);
+        const int32_t s = w1 < en.x ? (int32_t)col : (int32_t)en.y;
+        if (s != src) return s;
+    }
+    return negative_of(take_word(c, t, key), src, n - 1);
+}
+
 // Force on i from the attraction of Table 1 (t-FDP): pulls i toward the
 // partner, coefficient alpha (1 + beta / (1 + r^2)); d = y_i - y_partner.
 __device__ __forceinline__ float2 attraction_on_i(float dx, float dy) {
@@ -60,17 +107,13 @@ __device__ __forceinline__ float2 repulsion_on_i(float dx, float dy) {
 
 // Position accesses that must see other SMs' writes: cached in L2 only.
 __device__ __forceinline__ float2 load_pos(const float2 *p) { return __ldcg(p); }
-#ifndef SNAP_STORE_EXCH
-#define SNAP_STORE_EXCH 0
-#endif
-__device__ __forceinline__ void store_pos(float2 *p, float2 v) {
-#if SNAP_STORE_EXCH
+__device__ __forceinline__ void store_pos(float2 *p, float2 v) { __stcg(p, v); }
+
+// The same write as one 64-bit atomic exchange (for addresses many lanes write).
+__device__ __forceinline__ void exchange_pos(float2 *p, float2 v) {
     unsigned long long bits;
     memcpy(&bits, &v, 8);
     atomicExch(reinterpret_cast<unsigned long long *>(p), bits);
-#else
-    __stcg(p, v);
-#endif
 }
 
 // The edge stream is read once per epoch: evict-first streaming loads.

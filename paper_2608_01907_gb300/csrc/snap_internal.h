@@ -65,6 +65,8 @@ struct SyncArgs {
     uint32_t *status;
     const int32_t *node_graph;   // batch only
     const GraphInfo *graphs;
+    const uint2 *alias;          // weighted negatives: n entries {threshold, alias (graph-local)}; else null
+    double *energy;              // actual energy of the epoch is added here (null: not computed)
 };
 
 // Oriented bundle list: entry {j, CSR index of (i, j), CSR index of (j, i), 0}
@@ -116,9 +118,18 @@ struct OrientedArgs {
     const int32_t *node_graph;   // batch only: graph of every vertex
     const GraphInfo *graphs;     // batch only
     float inflight_share;        // lanes in flight / slots (share of the chunks running at once)
+    const uint2 *alias;          // weighted negatives (alias table, graph-local ids); null: uniform
+    double *energy;              // actual energy of the epoch is added here (null: not computed)
 };
 
+// Dispatches on a.alias (weighted negatives, epoch_weighted.cu) and a.energy
+// (actual energy, epoch_energy.cu; single graphs only).
 cudaError_t launch_oriented_epoch(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+cudaError_t launch_oriented_weighted(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+cudaError_t launch_oriented_energy(const OrientedArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+int oriented_weighted_blocks_per_sm(int red_mode, int k, int block, int multi);
+int oriented_energy_blocks_per_sm(int red_mode, int k, int block, int weighted);
+
 
 // One job of a multi-handle epoch: a single-graph HOGWILD handle's device
 // arrays, its positions, and the epoch, step and seed it runs this launch.
@@ -135,6 +146,7 @@ struct JobDesc {
     uint32_t epoch;
     float eta;
     int32_t seg_len;
+    const uint2 *alias;     // the job's alias table, or null (uniform)
 };
 
 struct MultiArgs {
@@ -148,9 +160,13 @@ struct MultiArgs {
     float inflight_share;
 };
 
-cudaError_t launch_multi_epoch(const MultiArgs &a, int red_mode, int grid, int block, cudaStream_t s);
-int multi_blocks_per_sm(int red_mode, int k, int block);
-int oriented_blocks_per_sm(int red_mode, int k, int block, int multi);
+// weighted: some job of the launch draws weighted negatives.
+cudaError_t launch_multi_epoch(const MultiArgs &a, int red_mode, int weighted, int grid, int block,
+                               cudaStream_t s);
+int multi_blocks_per_sm(int red_mode, int weighted, int k, int block);
+cudaError_t launch_multi_weighted(const MultiArgs &a, int red_mode, int grid, int block, cudaStream_t s);
+int multi_weighted_blocks_per_sm(int red_mode, int k, int block);
+int oriented_blocks_per_sm(int red_mode, int k, int block, int multi, int weighted);
 cudaError_t launch_sync_chunk(const SyncArgs &a, int grid, int block, cudaStream_t s);
 // y += eta * D * 2^-32 (clipped to `limit` when > 0), D = 0.  For a batch
 // (graphs != nullptr) eta and the clip come from each vertex's graph at
@@ -187,14 +203,17 @@ cudaError_t launch_objective_edges(const int64_t *row_ptr, const int32_t *col_id
 cudaError_t launch_objective_oriented(const int64_t *row_ptr, const int4 *ent, const int2 *meta,
                                       const ChunkLayout &L, int64_t nnz, const float2 *pos, double *partial,
                                       int grid, cudaStream_t s);
-cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, int32_t n,
+// Pair sums of the objective; wt (nullable) holds the per-vertex factors of
+// a weighted sampler ({x, y, z}: d_i P(j|i) = x_i z_j + y_i).
+// Exact: sum over ordered pairs i != j of coef_ij U^r, coef = d_i + d_j or c_ij.
+cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, const float4 *wt, int32_t n,
                                          double *partial, int grid, cudaStream_t s);
-// Batch: sum over graphs of (1 / (2 (n_g - 1))) * sum over ordered pairs of the
-// graph of (d_i + d_j) U^r; the host applies k / 2.
-cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const int32_t *node_graph,
-                                         const GraphInfo *graphs, int32_t n, double *partial, int grid,
-                                         cudaStream_t s);
-cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, int32_t n,
+// Batch: sum over graphs and ordered pairs of the graph of w_ij U^r, w_ij =
+// (d_i + d_j) / (2 (n_g - 1)) or c_ij / 2; the host applies k / 2.
+cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const float4 *wt,
+                                         const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
+                                         double *partial, int grid, cudaStream_t s);
+cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, const float4 *wt, int32_t n,
                                            int64_t pairs, uint64_t seed, double *partial, int grid,
                                            cudaStream_t s);
 

@@ -94,8 +94,10 @@ def test_host_side_argument_errors(lib):
     st, msg = _status(snap.snap_layout_create, g.row_ptr, g.col_idx, deg)
     assert st == 1 and "degrees[3]" in msg
     assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, None, 0)[0] == 1
-    o = snap.make_options(sampler=snap.SAMPLER_DEGREE)
-    assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)[0] == 5
+    o = snap.make_options(sampler=snap.SAMPLER_WEIGHTS)          # no node_weights
+    assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)[0] == 1
+    o = snap.make_options(sampler=3)
+    assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)[0] == 1
     for bad in (dict(mode=7), dict(sync_substeps=0), dict(segment_edges=6), dict(block_threads=48),
                 dict(sync_cap=-1.0), dict(block_threads=512), dict(max_inflight=1.5)):
         assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=snap.make_options(**bad))[0] == 1, bad
