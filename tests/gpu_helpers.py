@@ -23,6 +23,44 @@ def schedule_dict(s: snap.SnapSchedule) -> dict:
     return dict(kind=s.kind, eta0=s.eta0, eta_min=s.eta_min, total_epochs=s.total_epochs)
 
 
+def _row_position(q: int, L: int) -> int:
+    """Stored position of the rank-q entry of an oriented row of length L:
+    (a q) mod L, a the odd number from floor(0.618 L) | 1 upwards coprime with L."""
+    from math import gcd
+    if L <= 2:
+        return q
+    a = int(0.6180339887498949 * L) | 1
+    while gcd(a, L) != 1:
+        a += 2
+    return (a * q) % L
+
+
+def oriented_order(g) -> np.ndarray:
+    """Visiting order of the directed CSR edges by one Hogwild lane (built
+    here from the documented rule, independently of the library): every
+    undirected edge in the row of its higher-ranked endpoint (degree, then
+    smaller id); a row's entries in ascending partner id, then stored at
+    _row_position; rows in vertex order; per entry (i, j) then (j, i)."""
+    rp, ci = g.row_ptr, g.col_idx
+    deg = np.diff(rp)
+    order = []
+    for i in range(g.n):
+        row = []
+        for e in range(rp[i], rp[i + 1]):
+            j = ci[e]
+            if deg[i] > deg[j] or (deg[i] == deg[j] and i < j):
+                rev = rp[j] + int(np.searchsorted(ci[rp[j]:rp[j + 1]], i))
+                assert ci[rev] == i
+                row.append((e, rev))
+        placed = [None] * len(row)
+        for q, pair in enumerate(row):
+            placed[_row_position(q, len(row))] = pair
+        for e, rev in placed:
+            order += [e, rev]
+    assert sorted(order) == list(range(g.nnz))
+    return np.array(order, dtype=np.int64)
+
+
 def gpu_layout(torch, g, Y0, epochs, k, sched, seed, opts=None, epoch_begin=0):
     """Runs epochs on the GPU through the C ABI; returns the float32 positions."""
     pos = torch.from_numpy(np.ascontiguousarray(Y0, dtype=np.float32)).cuda()

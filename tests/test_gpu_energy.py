@@ -6,22 +6,10 @@ import pytest
 
 import oracle
 import paper_2608_01907_gb300 as snap
-from gpu_helpers import schedule_dict
+from gpu_helpers import oriented_order, schedule_dict
 from synth import initial_positions, sbm_graph, tiny_graph
 
 pytestmark = pytest.mark.gpu
-
-
-def _oriented_order(g):
-    rp, ci = g.row_ptr, g.col_idx
-    deg = np.diff(rp)
-    order = []
-    for i in range(g.n):
-        for e in range(rp[i], rp[i + 1]):
-            j = ci[e]
-            if deg[i] > deg[j] or (deg[i] == deg[j] and i < j):
-                order += [e, rp[j] + int(np.searchsorted(ci[rp[j]:rp[j + 1]], i))]
-    return np.array(order, dtype=np.int64)
 
 
 def _gpu_energy(torch, g, Y0, epochs, k, sched, seed, opts):
@@ -44,7 +32,7 @@ def test_single_lane_energy_equals_oracle(cuda, mode, sampler, k):
     _, got = _gpu_energy(cuda, g, Y0, 3, k, sched, 8, opts)
     sam = oracle.Sampler.degree(g.row_ptr) if sampler == snap.SAMPLER_DEGREE else None
     _, ref = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 3, k, schedule_dict(sched), seed=8,
-                        order=_oriented_order(g), return_energy=True, sampler=sam)
+                        order=oriented_order(g), return_energy=True, sampler=sam)
     print(f"energy mode={mode} sampler={sampler} k={k}: {got} vs {ref}")
     assert np.allclose(got, ref, rtol=1e-4)
 

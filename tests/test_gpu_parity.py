@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import paper_2608_01907_gb300 as snap
-from gpu_helpers import SYNC_RTOL, gpu_layout, parity_error, schedule_dict
+from gpu_helpers import SYNC_RTOL, gpu_layout, oriented_order, parity_error, schedule_dict
 from synth import Graph, edges_to_csr, initial_positions, sbm_graph, tiny_graph
 
 pytestmark = pytest.mark.gpu
@@ -80,27 +80,11 @@ def test_sync_is_bitwise_deterministic_and_resumable(cuda):
 
 
 # --------------------------------------------------------------------------
-# Hogwild with a single segment: one lane runs Algorithm 1 over the oriented
+# Hogwild with a single chunk: one lane runs Algorithm 1 over the oriented
 # bundles -- each undirected edge in the row of its higher-ranked endpoint
-# (degree, then smaller id), directions (i, j) then (j, i)
+# (degree, then smaller id), directions (i, j) then (j, i) (gpu_helpers.
+# oriented_order)
 # --------------------------------------------------------------------------
-def oriented_order(g):
-    """Visiting order of the directed CSR edges by one lane (built here from
-    the rule, independently of the library)."""
-    rp, ci = g.row_ptr, g.col_idx
-    deg = np.diff(rp)
-    order = []
-    for i in range(g.n):
-        for e in range(rp[i], rp[i + 1]):
-            j = ci[e]
-            if deg[i] > deg[j] or (deg[i] == deg[j] and i < j):
-                rev = rp[j] + int(np.searchsorted(ci[rp[j]:rp[j + 1]], i))
-                assert ci[rev] == i
-                order += [e, rev]
-    assert sorted(order) == list(range(g.nnz))
-    return np.array(order, dtype=np.int64)
-
-
 @pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
 @pytest.mark.parametrize("n,m,k", [(2, 0, 0), (2, 0, 1), (5, 6, 3), (12, 30, 5), (40, 120, 3), (90, 300, 10),
                                    (300, 900, 4), (60, 0, 2)])

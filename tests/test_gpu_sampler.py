@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import paper_2608_01907_gb300 as snap
-from gpu_helpers import SYNC_RTOL, gpu_layout, parity_error, schedule_dict
+from gpu_helpers import SYNC_RTOL, gpu_layout, oriented_order, parity_error, schedule_dict
 from synth import batch_sbm_graphs, initial_positions, sbm_graph, tiny_graph
 
 pytestmark = pytest.mark.gpu
@@ -43,19 +43,6 @@ def test_weighted_sync_matches_oracle_after_one_epoch(cuda, kind, name, k, S):
     assert err < SYNC_RTOL
 
 
-def _oriented_order(g):
-    rp, ci = g.row_ptr, g.col_idx
-    deg = np.diff(rp)
-    order = []
-    for i in range(g.n):
-        for e in range(rp[i], rp[i + 1]):
-            j = ci[e]
-            if deg[i] > deg[j] or (deg[i] == deg[j] and i < j):
-                rev = rp[j] + int(np.searchsorted(ci[rp[j]:rp[j + 1]], i))
-                order += [e, rev]
-    return np.array(order, dtype=np.int64)
-
-
 @pytest.mark.parametrize("kind", ["degree", "weights"])
 @pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
 @pytest.mark.parametrize("n,m,k", [(12, 30, 5), (90, 300, 10), (300, 900, 3)])
@@ -65,7 +52,7 @@ def test_weighted_single_lane_is_algorithm1_in_oriented_order(cuda, kind, mode, 
     Y0 = initial_positions(g.n, 4)
     sched = snap.linear_schedule(eta0=0.5, total_epochs=4)
     got = gpu_layout(cuda, g, Y0, 2, k, sched, seed=21, opts=snap.make_options(mode=mode, segment_edges=4096, **kw))
-    ref = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 2, k, schedule_dict(sched), seed=21, order=_oriented_order(g),
+    ref = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 2, k, schedule_dict(sched), seed=21, order=oriented_order(g),
                      sampler=sam)
     err = parity_error(got, ref)
     print(f"weighted single lane {kind} mode={mode} n={n} k={k}: max rel err {err:.2e}")
