@@ -1,6 +1,7 @@
 """Benchmark: 30-epoch SNAP-tFDP layouts of a 4,194,304-node / 34,000,000-edge
 R-MAT graph (a=0.57, b=c=0.19, degree-sorted BFS relabelling), k = 3
-negatives, Hogwild mode, on one GB300.
+negatives, lock-free Hogwild epochs (default HOGWILD_RED: racy reads and
+atomic float adds; --mode hogwild: racy stores), on one GB300.
 
 One step = one whole 30-epoch layout (30 epoch launches) starting from the
 same initial positions; the metric is pair updates per second, one update
@@ -45,7 +46,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="snap", choices=["snap", "reference"])
     p.add_argument("--k", type=int, default=3)
-    p.add_argument("--mode", default="hogwild", choices=["hogwild", "hogwild_red", "sync"])
+    p.add_argument("--mode", default="hogwild_red", choices=["hogwild", "hogwild_red", "sync"],
+                   help="hogwild_red (default): racy reads, atomic float adds (HOGWILD!); hogwild: racy stores")
     p.add_argument("--sampler", default="uniform", choices=["uniform", "degree"],
                    help="negatives: uniform (the paper's) or degree-weighted (alias table)")
     p.add_argument("--scale", type=int, default=22)
@@ -530,7 +532,7 @@ def run_batch(args, rank, world, local_rank):
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch-sbm-{offs.size - 1}-graphs-k{k}-{EPOCHS}ep", "graphs": int(offs.size - 1),
-                       "n_total": n, "undirected_edges": nnz // 2, "mode": "hogwild"},
+                       "n_total": n, "undirected_edges": nnz // 2, "mode": "hogwild_red"},
             "one_graph_per_launch": {"updates_per_s": upd_pg / (ms_pg / 1e3), "graphs_timed": len(handles),
                                      "launches": len(handles) * EPOCHS, "ms": ms_pg},
             "speedup_vs_one_graph_per_launch": (updates / (ms / 1e3)) / (upd_pg / (ms_pg / 1e3)),
@@ -619,7 +621,7 @@ def run_serve(args, rank, world, local_rank):
             "config": {"workload": f"serve-poisson{args.serve_rate:g}-{len(arrivals)}jobs-{EPOCHS}ep-k{k}",
                        "jobs": len(arrivals), "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
                        "graph_pool": "48 graphs: R-MAT / 8-community planted partition, |E| log-uniform 1k-2M",
-                       "mode": "hogwild"},
+                       "mode": "hogwild_red"},
             "continuous_batching": srv, "one_job_at_a_time": seq,
             "p99_speedup": seq["p99_s"] / srv["p99_s"], "throughput_ratio": srv["updates_per_s"] / seq["updates_per_s"],
             "all_finite": finite, "clocks": clk}

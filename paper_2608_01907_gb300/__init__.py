@@ -168,7 +168,7 @@ def snap_options_default() -> SnapOptions:
     return o
 
 
-def make_options(mode: int = MODE_HOGWILD, sync_substeps: int = 1, sync_cap: float = 0.0,
+def make_options(mode: int = MODE_HOGWILD_RED, sync_substeps: int = 1, sync_cap: float = 0.0,
                  segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM,
                  cuda_graph: bool = False, max_inflight: float = 0.0, node_weights=None) -> SnapOptions:
     """Options for snap_layout_create; node_weights (n floats) goes with SAMPLER_WEIGHTS

@@ -416,7 +416,7 @@ extern "C" {
 void snap_options_default(snap_options *o) {
     if (!o) return;
     memset(o, 0, sizeof(*o));
-    o->mode = SNAP_MODE_HOGWILD;
+    o->mode = SNAP_MODE_HOGWILD_RED;
     o->sampler = SNAP_SAMPLER_UNIFORM;
     o->node_weights = nullptr;
     o->sync_substeps = 1;

@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (MODE_HOGWILD, MultiEpoch, SnapSchedule, linear_schedule, make_options, snap_layout_create,
+from . import (MODE_HOGWILD_RED, MultiEpoch, SnapSchedule, linear_schedule, make_options, snap_layout_create,
                snap_layout_destroy, snap_layout_device_bytes)
 
 
@@ -61,7 +61,7 @@ class Job:
 
 class LayoutServer:
     def __init__(self, hbm_budget: int, max_jobs: int = 256, epochs: int = 30, neg_samples: int = 3,
-                 eta0: float = 1.0, mode: int = MODE_HOGWILD, segment_edges: int = 0, stream=None,
+                 eta0: float = 1.0, mode: int = MODE_HOGWILD_RED, segment_edges: int = 0, stream=None,
                  clock=time.perf_counter):
         import torch
         self.torch = torch
@@ -167,7 +167,7 @@ class LayoutServer:
         self.multi.close()
 
 
-def run_sequential(jobs, epochs: int = 30, neg_samples: int = 3, eta0: float = 1.0, mode: int = MODE_HOGWILD,
+def run_sequential(jobs, epochs: int = 30, neg_samples: int = 3, eta0: float = 1.0, mode: int = MODE_HOGWILD_RED,
                    stream=None, clock=time.perf_counter, arrivals=None):
     """The plain form: one job at a time, first come first served, each laid
     out completely (create, 30 epoch launches, copy back) before the next."""

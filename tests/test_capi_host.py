@@ -70,7 +70,7 @@ int main(void) {
 def test_options_default(lib):
     o = snap.snap_options_default()
     assert (o.mode, o.sampler, o.sync_substeps, o.sync_cap, o.segment_edges, o.block_threads, o.flags) == \
-        (0, 0, 1, 0.0, 0, 0, 0)
+        (snap.MODE_HOGWILD_RED, snap.SAMPLER_UNIFORM, 1, 0.0, 0, 0, 0)
 
 
 def _status(fn, *a, **kw):
