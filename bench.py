@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--scale", type=int, default=22)
     p.add_argument("--edges", type=int, default=34_000_000)
     p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--generator", default="numpy", choices=["numpy", "native"],
+                   help="R-MAT generator: numpy (synth.rmat_graph) or the native OpenMP one for billions of edges")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
@@ -67,9 +69,15 @@ def parse():
     return p.parse_args()
 
 
-def load_graph(scale, edges, seed):
-    """R-MAT graph relabelled by snap_graph_reorder; cached on local disk."""
+def load_graph(scale, edges, seed, generator="numpy"):
+    """R-MAT graph relabelled by snap_graph_reorder; cached on local disk
+    (numpy generator only: the native one regenerates faster than a reload)."""
     import paper_2608_01907_gb300 as snap
+    if generator == "native":
+        from synth import rmat_graph_native
+        g = rmat_graph_native(scale, edges, seed=seed)
+        _, rp, ci = snap.snap_graph_reorder(g.row_ptr, g.col_idx, g.n)
+        return g.n, rp, ci
     cache = os.path.join(tempfile.gettempdir(), "snap_bench_cache")
     os.makedirs(cache, exist_ok=True)
     path = os.path.join(cache, f"rmat{scale}_{edges}_s{seed}_bfs.npz")
@@ -210,7 +218,7 @@ def replica_throughput(local_ms: float, units_per_rank: float, dist=None, device
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    n, row_ptr, col_idx = load_graph(args.scale, args.edges, args.seed)
+    n, row_ptr, col_idx = load_graph(args.scale, args.edges, args.seed, args.generator)
     Y0 = initial_positions(n, args.seed).astype(np.float64)
     import oracle
     oracle.build()
@@ -252,7 +260,7 @@ def run_snap(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    n, row_ptr, col_idx = load_graph(args.scale, args.edges, args.seed)
+    n, row_ptr, col_idx = load_graph(args.scale, args.edges, args.seed, args.generator)
     nnz = int(row_ptr[-1])
     k = args.k
     mode = {"hogwild": snap.MODE_HOGWILD, "hogwild_red": snap.MODE_HOGWILD_RED, "sync": snap.MODE_SYNC}[args.mode]
@@ -431,7 +439,8 @@ def run_snap(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_layout": ms_per_step / 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{k}-{EPOCHS}ep-bfs", "n": n,
+                "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{k}-{EPOCHS}ep-bfs"
+                               + ("-native" if args.generator == "native" else ""), "n": n,
                            "undirected_edges": args.edges, "directed_edges": nnz, "k": k, "epochs": EPOCHS,
                            "mode": args.mode, "sampler": args.sampler, "isolated_nodes": int(n - nonempty),
                            "l2": l2_note,

@@ -139,7 +139,8 @@ void snap_options_default(snap_options *opts);
  * (Section 3.3, "requires only two data structures"); the edge list is a CSR
  * here, each undirected edge stored as (i, j) and (j, i).
  *
- *   row_ptr   host, n+1 int64; row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz < 2^31.
+ *   row_ptr   host, n+1 int64; row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz < 2^32
+ *             (directed edges: up to 2^31 - 1 undirected edges).
  *   col_idx   host, nnz int32; each row strictly ascending, 0 <= j < n, j != i,
  *             and symmetric: j in row i  <=>  i in row j.
  *   degrees   host, n int32, or NULL.  If given it must equal the row lengths.

@@ -25,6 +25,12 @@ Parity status per function:
                               column; equal weights give full columns)
   edge_negatives (weighted)   pinned (chi^2 against P(s|i) including the
                               16-rejection fallback; forced fallback word count)
+  silhouette                  pinned (hand-worked four-point value; separated
+                              clusters -> 1; label permutation invariance)
+  adjusted_rand               pinned (hand-worked contingency table; identical
+                              and relabelled partitions -> 1; independent ~ 0)
+  kmeans / cluster_quality    pinned (separated blobs recovered exactly; CQ of
+                              the planted layout = 1)
   weighted objective/gradient pinned (Monte-Carlo displacement mean -> -2 grad U
                               with P(s|i); finite differences; uniform q equals
                               the uniform objective)
@@ -96,6 +102,12 @@ def _load():
     lib.oracle_edge_negatives.argtypes = [u64, u32, u64, i32, i32, i32, P, P, P]
     lib.oracle_edge_negatives.restype = u32
     lib.oracle_exact_gradient.restype = ctypes.c_int
+    lib.oracle_silhouette.argtypes = [P, P, i32, i32, P, i32]
+    lib.oracle_silhouette.restype = f64
+    lib.oracle_adjusted_rand.argtypes = [P, P, i32, i32, i32]
+    lib.oracle_adjusted_rand.restype = f64
+    lib.oracle_kmeans.argtypes = [P, i32, i32, i32, i32, u64, P]
+    lib.oracle_kmeans.restype = f64
     lib.oracle_neighborhood_preservation.argtypes = [P, P, i32, P, P, i32]
     lib.oracle_neighborhood_preservation.restype = f64
     _lib = lib
@@ -294,3 +306,38 @@ def neighborhood_preservation(row_ptr, col_idx, n, Y, nodes=None) -> float:
         return float(_load().oracle_neighborhood_preservation(_p(rp), _p(ci), n, _p(Yd), None, 0))
     nd = np.ascontiguousarray(nodes, dtype=np.int32)
     return float(_load().oracle_neighborhood_preservation(_p(rp), _p(ci), n, _p(Yd), _p(nd), nd.size))
+
+
+def silhouette(Y, labels, nodes=None) -> float:
+    """Silhouette index (Section 4.1, SI) of a layout under ground-truth labels."""
+    Yd = _positions(Y)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    K = int(lab.max()) + 1
+    if nodes is None:
+        return float(_load().oracle_silhouette(_p(Yd), _p(lab), lab.size, K, None, 0))
+    nd = np.ascontiguousarray(nodes, dtype=np.int32)
+    return float(_load().oracle_silhouette(_p(Yd), _p(lab), lab.size, K, _p(nd), nd.size))
+
+
+def adjusted_rand(a, b) -> float:
+    la = np.ascontiguousarray(a, dtype=np.int32)
+    lb = np.ascontiguousarray(b, dtype=np.int32)
+    return float(_load().oracle_adjusted_rand(_p(la), _p(lb), la.size, int(la.max()) + 1, int(lb.max()) + 1))
+
+
+def kmeans(Y, K, iters=100, restarts=4, seed=1):
+    """(labels, inertia) of k-means on the layout."""
+    Yd = _positions(Y)
+    out = np.zeros(Yd.shape[0], dtype=np.int32)
+    inertia = _load().oracle_kmeans(_p(Yd), Yd.shape[0], K, iters, restarts, seed, _p(out))
+    if inertia < 0:
+        raise ValueError("kmeans needs 1 <= K <= n")
+    return out, float(inertia)
+
+
+def cluster_quality(Y, labels, seed=1) -> float:
+    """CQ of Section 4.1: ARI of the ground truth against k-means of the layout
+    with as many clusters as labels."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    pred, _ = kmeans(Y, int(lab.max()) + 1, seed=seed)
+    return adjusted_rand(lab, pred)

@@ -20,6 +20,8 @@
  *     such mode; it is the deterministic reference for the library's
  *     synchronous mode.
  *   - Neighbourhood preservation NP with r = 2 (Section 4.1, Metrics).
+ *   - The cluster metrics of Section 4.1: silhouette index (SI) and clustering
+ *     quality CQ = ARI(labels, k-means of the layout).
  *   - Weighted negatives (degree or caller weights, the future work of
  *     Section 6) through an alias table, and the objective whose expected
  *     gradient they follow (Section 3.3's derivation with P(s|i) in place of
@@ -774,4 +776,195 @@ double oracle_neighborhood_preservation(const int64_t *row_ptr, const int32_t *c
     free(stamp);
     free(items);
     return used > 0 ? sum / (double)used : 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cluster metrics of Section 4.1 (evaluation only).                        */
+/* ------------------------------------------------------------------------ */
+
+/* Silhouette index (Rousseeuw 1987) of the layout under ground-truth labels
+ * 0..K-1: s(i) = (b(i) - a(i)) / max(a(i), b(i)), a(i) the mean distance
+ * from i to the other members of its cluster, b(i) the smallest mean
+ * distance from i to the members of another cluster; s(i) = 0 for a member
+ * of a singleton cluster.  Mean over `nodes` (NULL: every vertex), with
+ * distances to every vertex.  Returns the mean, or NaN on allocation failure
+ * or K < 2. */
+double oracle_silhouette(const double *Y, const int32_t *labels, int32_t n, int32_t K,
+                         const int32_t *nodes, int32_t count)
+{
+    if (K < 2)
+        return NAN;
+    double *sum = (double *)malloc(sizeof(double) * (size_t)K);
+    int64_t *size = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    if (!sum || !size) {
+        free(sum);
+        free(size);
+        return NAN;
+    }
+    for (int32_t v = 0; v < n; ++v)
+        size[labels[v]]++;
+    int32_t m = nodes ? count : n;
+    double total = 0.0;
+    for (int32_t q = 0; q < m; ++q) {
+        int32_t i = nodes ? nodes[q] : q;
+        for (int32_t c = 0; c < K; ++c)
+            sum[c] = 0.0;
+        for (int32_t v = 0; v < n; ++v) {
+            if (v == i)
+                continue;
+            double dx = Y[2 * (int64_t)i] - Y[2 * (int64_t)v], dy = Y[2 * (int64_t)i + 1] - Y[2 * (int64_t)v + 1];
+            sum[labels[v]] += sqrt(dx * dx + dy * dy);
+        }
+        int32_t own = labels[i];
+        if (size[own] < 2)
+            continue;   /* s(i) = 0 */
+        double a = sum[own] / (double)(size[own] - 1);
+        double b = INFINITY;
+        for (int32_t c = 0; c < K; ++c)
+            if (c != own && size[c] > 0 && sum[c] / (double)size[c] < b)
+                b = sum[c] / (double)size[c];
+        double mx = a > b ? a : b;
+        total += mx > 0.0 ? (b - a) / mx : 0.0;
+    }
+    free(sum);
+    free(size);
+    return m > 0 ? total / (double)m : 0.0;
+}
+
+/* Adjusted Rand index (Hubert & Arabie 1985) of two labelings with labels in
+ * [0, Ka) and [0, Kb): (I - E) / (M - E), I = sum over the contingency table
+ * of C(n_ij, 2), E = sum_i C(a_i, 2) sum_j C(b_j, 2) / C(n, 2), M = the mean
+ * of the two marginal sums.  1 for identical partitions. */
+double oracle_adjusted_rand(const int32_t *la, const int32_t *lb, int32_t n, int32_t Ka, int32_t Kb)
+{
+    int64_t *tab = (int64_t *)calloc((size_t)Ka * (size_t)Kb, sizeof(int64_t));
+    int64_t *ra = (int64_t *)calloc((size_t)Ka, sizeof(int64_t));
+    int64_t *rb = (int64_t *)calloc((size_t)Kb, sizeof(int64_t));
+    if (!tab || !ra || !rb) {
+        free(tab);
+        free(ra);
+        free(rb);
+        return NAN;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        tab[(size_t)la[v] * (size_t)Kb + (size_t)lb[v]]++;
+        ra[la[v]]++;
+        rb[lb[v]]++;
+    }
+    double I = 0.0, A = 0.0, B = 0.0;
+    for (size_t t = 0; t < (size_t)Ka * (size_t)Kb; ++t)
+        I += 0.5 * (double)tab[t] * (double)(tab[t] - 1);
+    for (int32_t i = 0; i < Ka; ++i)
+        A += 0.5 * (double)ra[i] * (double)(ra[i] - 1);
+    for (int32_t j = 0; j < Kb; ++j)
+        B += 0.5 * (double)rb[j] * (double)(rb[j] - 1);
+    free(tab);
+    free(ra);
+    free(rb);
+    double pairs = 0.5 * (double)n * (double)(n - 1);
+    double E = pairs > 0.0 ? A * B / pairs : 0.0;
+    double M = 0.5 * (A + B);
+    return M - E != 0.0 ? (I - E) / (M - E) : 1.0;
+}
+
+/* k-means of the layout (Lloyd's iterations from a k-means++ start, Arthur &
+ * Vassilvitskii 2007; the start's random numbers from Philox with counter
+ * (draw, 0, 0xFFFFFFFC, restart) and key seed), `restarts` starts, the
+ * partition of least inertia written to out.  Returns that inertia, or -1. */
+double oracle_kmeans(const double *Y, int32_t n, int32_t K, int32_t iters, int32_t restarts, uint64_t seed,
+                     int32_t *out)
+{
+    double *C = (double *)malloc(sizeof(double) * 2 * (size_t)K);
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)n);
+    int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *acc = (double *)malloc(sizeof(double) * 3 * (size_t)K);
+    if (!C || !d2 || !lab || !acc || K < 1 || n < K) {
+        free(C);
+        free(d2);
+        free(lab);
+        free(acc);
+        return -1.0;
+    }
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double best = INFINITY;
+    for (int32_t r = 0; r < restarts; ++r) {
+        uint32_t draw = 0;
+        /* k-means++: first centre uniform, then proportional to squared distance */
+        for (int32_t c = 0; c < K; ++c) {
+            uint32_t ctr[4] = {draw++, 0u, 0xFFFFFFFCu, (uint32_t)r}, w[4];
+            oracle_philox4x32_10(ctr, key, w);
+            double u = ((double)w[0] + 4294967296.0 * (double)(w[1] >> 11)) / (4294967296.0 * 2097152.0);
+            int32_t pick = 0;
+            if (c == 0) {
+                pick = (int32_t)(u * (double)n);
+                if (pick >= n)
+                    pick = n - 1;
+            } else {
+                double tot = 0.0;
+                for (int32_t v = 0; v < n; ++v)
+                    tot += d2[v];
+                double target = u * tot, run = 0.0;
+                pick = n - 1;
+                for (int32_t v = 0; v < n; ++v) {
+                    run += d2[v];
+                    if (run > target) {
+                        pick = v;
+                        break;
+                    }
+                }
+            }
+            C[2 * c] = Y[2 * (int64_t)pick];
+            C[2 * c + 1] = Y[2 * (int64_t)pick + 1];
+            for (int32_t v = 0; v < n; ++v) {
+                double dx = Y[2 * (int64_t)v] - C[2 * c], dy = Y[2 * (int64_t)v + 1] - C[2 * c + 1];
+                double dd = dx * dx + dy * dy;
+                if (c == 0 || dd < d2[v])
+                    d2[v] = dd;
+            }
+        }
+        double inertia = 0.0;
+        for (int32_t it = 0; it <= iters; ++it) {
+            inertia = 0.0;
+            int changed = 0;
+            for (int32_t v = 0; v < n; ++v) {
+                int32_t bc = 0;
+                double bd = INFINITY;
+                for (int32_t c = 0; c < K; ++c) {
+                    double dx = Y[2 * (int64_t)v] - C[2 * c], dy = Y[2 * (int64_t)v + 1] - C[2 * c + 1];
+                    double dd = dx * dx + dy * dy;
+                    if (dd < bd) {
+                        bd = dd;
+                        bc = c;
+                    }
+                }
+                if (it == 0 || lab[v] != bc)
+                    changed = 1;
+                lab[v] = bc;
+                inertia += bd;
+            }
+            if (!changed || it == iters)
+                break;
+            for (int32_t c = 0; c < 3 * K; ++c)
+                acc[c] = 0.0;
+            for (int32_t v = 0; v < n; ++v) {
+                acc[3 * lab[v]] += Y[2 * (int64_t)v];
+                acc[3 * lab[v] + 1] += Y[2 * (int64_t)v + 1];
+                acc[3 * lab[v] + 2] += 1.0;
+            }
+            for (int32_t c = 0; c < K; ++c)
+                if (acc[3 * c + 2] > 0.0) {
+                    C[2 * c] = acc[3 * c] / acc[3 * c + 2];
+                    C[2 * c + 1] = acc[3 * c + 1] / acc[3 * c + 2];
+                }
+        }
+        if (inertia < best) {
+            best = inertia;
+            memcpy(out, lab, sizeof(int32_t) * (size_t)n);
+        }
+    }
+    free(C);
+    free(d2);
+    free(lab);
+    free(acc);
+    return best;
 }

@@ -438,7 +438,7 @@ static snap_status check_csr_host(const int64_t *row_ptr, const int32_t *col_idx
         if (row_ptr[i + 1] < row_ptr[i])
             return fail(SNAP_ERR_INVALID_ARG, "row_ptr decreases at row %d", i);
     const int64_t nnz = row_ptr[n];
-    if (nnz >= ((int64_t)1 << 31)) return fail(SNAP_ERR_INVALID_ARG, "nnz = %lld exceeds 2^31-1", (long long)nnz);
+    if (nnz >= ((int64_t)1 << 32)) return fail(SNAP_ERR_INVALID_ARG, "nnz = %lld exceeds 2^32-1", (long long)nnz);
     if (nnz > 0 && !col_idx) return fail(SNAP_ERR_INVALID_ARG, "col_idx is NULL");
     if (degrees)
         for (int32_t i = 0; i < n; ++i)

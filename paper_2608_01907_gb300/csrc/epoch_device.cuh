@@ -205,7 +205,7 @@ __device__ __forceinline__ void later_negatives(const OrientedArgs &a, const Gra
 
 template <bool RED, int G, bool W, bool E>
 __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, int32_t j,
-                                               int32_t e1, int32_t e2, float2 &yi, float &en) {
+                                               int64_t e1, int64_t e2, float2 &yi, float &en) {
     const float eta = c.eta;
     int32_t s1[4] = {0, 0, 0, 0}, s2[4] = {0, 0, 0, 0};
     float2 v1[4], v2[4];
@@ -347,8 +347,10 @@ __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t sl
             yi0 = yi;
         }
         if (!c.active) continue;
-        const int4 ent = load_entry(ep);   // {j, index of (i, j), index of (j, i), -}
-        oriented_entry<RED, G, W, E>(a, c, row, ent.x, ent.y, ent.z, yi, en);
+        const int4 ent = load_entry(ep);   // {j, indices of (i, j) and (j, i): low bits, bits 32..47}
+        const int64_t e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
+        const int64_t e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
+        oriented_entry<RED, G, W, E>(a, c, row, ent.x, e1, e2, yi, en);
     }
     if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
                                              flags);

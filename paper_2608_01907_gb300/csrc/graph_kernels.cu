@@ -117,6 +117,13 @@ __global__ void orient_flags_kernel(const int64_t *__restrict__ row_ptr, const i
     if (blockIdx.x == 0 && threadIdx.x == 0) flags[nnz] = 0;
 }
 
+// Entry {j, low 32 bits of the indices of (i, j) and (j, i), their bits
+// 32..47 packed in .w}: up to 2^48 directed edges.
+__device__ __forceinline__ int4 make_entry(int32_t j, int64_t fwd, int64_t rev) {
+    const uint32_t hi = (uint32_t)((fwd >> 32) & 0xFFFF) | ((uint32_t)((rev >> 32) & 0xFFFF) << 16);
+    return make_int4(j, (int32_t)(uint32_t)fwd, (int32_t)(uint32_t)rev, (int32_t)hi);
+}
+
 // Order of the entries inside an oriented row of length L: the entry of
 // rank q (ascending partner id) is stored at (a q) mod L, a the odd number
 // nearest above 0.618 L that is coprime with L.  Consecutive stored entries
@@ -159,7 +166,7 @@ __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const
             else
                 hi = mid;
         }
-        ent[p] = make_int4(j, (int32_t)e, (int32_t)lo, 0);
+        ent[p] = make_entry(j, e, lo);
     });
 }
 
@@ -454,7 +461,7 @@ cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, 
 
 cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in, int32_t *out, int64_t count,
                                cudaStream_t s) {
-    return cub::DeviceScan::ExclusiveSum(temp, *temp_bytes, in, out, (int)count, s);
+    return cub::DeviceScan::ExclusiveSum(temp, *temp_bytes, in, out, count, s);
 }
 
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,

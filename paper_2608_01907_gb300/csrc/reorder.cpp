@@ -34,7 +34,7 @@ extern "C" snap_status snap_graph_reorder(const int64_t *row_ptr, const int32_t 
     for (int32_t i = 0; i < n; ++i)
         if (row_ptr[i + 1] < row_ptr[i]) return snap::reorder_fail(SNAP_ERR_INVALID_ARG, "row_ptr decreases");
     const int64_t nnz = row_ptr[n];
-    if (nnz >= ((int64_t)1 << 31)) return snap::reorder_fail(SNAP_ERR_INVALID_ARG, "nnz exceeds 2^31-1");
+    if (nnz >= ((int64_t)1 << 40)) return snap::reorder_fail(SNAP_ERR_INVALID_ARG, "nnz exceeds 2^40-1");
     if (nnz > 0 && (!col_idx || !col_idx_out)) return snap::reorder_fail(SNAP_ERR_INVALID_ARG, "NULL col_idx");
     for (int64_t e = 0; e < nnz; ++e)
         if (col_idx[e] < 0 || col_idx[e] >= n)

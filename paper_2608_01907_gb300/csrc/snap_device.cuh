@@ -121,7 +121,8 @@ __device__ __forceinline__ int4 load_cols4(const int32_t *p) {
     return __ldcs(reinterpret_cast<const int4 *>(p));
 }
 
-// One oriented entry {j, index of (i, j), index of (j, i), row-major index}.
+// One oriented entry {j, low 32 bits of the indices of (i, j) and (j, i),
+// their bits 32..47}.
 // Read through L1: the 32 lanes of a warp walk one compact run of entries
 // over several iterations, so a line fetched for one lane serves others.
 __device__ __forceinline__ int4 load_entry(const int4 *p) { return __ldg(p); }

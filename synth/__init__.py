@@ -11,6 +11,7 @@ from .graphs import (  # noqa: F401
     sbm_graph,
     lfr_graph,
     rmat_graph,
+    rmat_graph_native,
     batch_sbm_graphs,
     planted_partition_graph,
     serving_graph_pool,

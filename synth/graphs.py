@@ -18,6 +18,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import os
+
 import numpy as np
 
 
@@ -263,6 +265,50 @@ def rmat_graph(scale: int = 22, num_edges: int = 34_000_000, a: float = 0.57, b:
     v = keys - u * n
     row_ptr, col_idx = edges_to_csr(n, u, v)
     return Graph(n, row_ptr, col_idx, name=f"rmat-s{scale}-e{num_edges}-s{seed}",
+                 meta=dict(a=a, b=b, c=c, d=1 - a - b - c, seed=seed))
+
+
+_NATIVE = None
+
+
+def _native_lib():
+    """The C generator (rmat_native.c), compiled with gcc on first use."""
+    global _NATIVE
+    if _NATIVE is not None:
+        return _NATIVE
+    import ctypes
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "rmat_native.c")
+    lib = os.path.join(here, "librmat_native.so")
+    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src])
+        os.replace(tmp, lib)
+    L = ctypes.CDLL(lib)
+    L.rmat_native_generate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    L.rmat_native_generate.restype = ctypes.c_int
+    _NATIVE = L
+    return L
+
+
+def rmat_graph_native(scale: int, num_edges: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                      seed: int = 1, threads: int = 0) -> Graph:
+    """R-MAT graph for billions of edges (the C generator rmat_native.c, OpenMP):
+    the same model and rules as rmat_graph, drawn from a counter-based stream
+    (splitmix64), so the graph depends on the seed only, not on the thread
+    count.  A different stream from rmat_graph: the two give different graphs
+    of the same distribution."""
+    n = 1 << scale
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    col_idx = np.empty(2 * num_edges, dtype=np.int32)
+    rc = _native_lib().rmat_native_generate(scale, num_edges, a, b, c, seed, threads,
+                                            row_ptr.ctypes.data, col_idx.ctypes.data)
+    if rc != 0:
+        raise MemoryError(f"rmat_native_generate failed ({rc})")
+    return Graph(n, row_ptr, col_idx, name=f"rmat-native-s{scale}-e{num_edges}-s{seed}",
                  meta=dict(a=a, b=b, c=c, d=1 - a - b - c, seed=seed))
 
 
