@@ -101,10 +101,16 @@ def measured_peak():
 
 
 def kernel_source_hash():
+    """Hash of the epoch kernel's code (comments and blank lines removed, so
+    that a comment edit does not orphan a recorded capture)."""
+    import re
     h = hashlib.sha256()
     for f in ("epoch_device.cuh", "epoch_kernels.cu", "snap_device.cuh", "snap_internal.h"):
-        with open(os.path.join(ROOT, "paper_2608_01907_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2608_01907_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*", "", line).strip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -7,8 +7,9 @@
 // HOGWILD modes work on oriented bundles (built by capi.cu at create):
 // every undirected edge {i, j} is listed once, in the row of its
 // higher-ranked endpoint (degree, then smaller id), with the CSR indices of
-// both directed copies.  The row-major list is cut into chunks of a few
-// entries, stored in a pseudo-random slot order; a warp takes one group of
+// both directed copies (a row's entries in a fixed affine order of their
+// partners, graph_kernels.cu).  The row-major list is cut into chunks of a
+// few entries, stored in a pseudo-random slot order; a warp takes one group of
 // 32 slots and the order of the groups is an affine permutation that changes
 // every epoch (the shuffle before bundling of Section 3.4).  A lane keeps
 // the source y_i of its current row in registers and applies both directed
