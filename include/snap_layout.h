@@ -150,9 +150,13 @@ void snap_options_default(snap_options *opts);
  *   out       receives the handle; untouched on error.
  *
  * Copies the CSR to the device (the host arrays may be freed on return),
- * checks it there, builds the per-lane segment table.  Synchronises the
- * stream.  Errors: INVALID_ARG (malformed input, with the first violation in
- * snap_last_error), OUT_OF_MEMORY, CUDA, NOT_SUPPORTED.
+ * checks it there and, in the HOGWILD modes, builds the oriented list (each
+ * undirected edge in the row of its higher-ranked endpoint, a row's entries
+ * in a fixed affine order of their partners, cut into chunks of
+ * segment_edges entries stored in a pseudo-random slot order) and frees the
+ * CSR; for a weighted sampler it also builds the alias table.  Synchronises
+ * the stream.  Errors: INVALID_ARG (malformed input, with the first
+ * violation in snap_last_error), OUT_OF_MEMORY, CUDA.
  */
 snap_status snap_layout_create(const int64_t *row_ptr, const int32_t *col_idx,
                                const int32_t *degrees, int32_t n,
@@ -193,8 +197,10 @@ snap_status snap_layout_create_batch(const int64_t *row_ptr, const int32_t *col_
  *   seed         keys the counter-based Philox4x32-10 stream: word w of edge
  *                e in epoch t is component w mod 4 of
  *                Philox(ctr = (e_lo, e_hi, t, w div 4), key = (seed_lo, seed_hi)).
- *                Negative m of edge e = (i, j) uses word m:
- *                u = floor(word * (n-1) / 2^32), s = u + (u >= i).
+ *                The negatives of edge e = (i, j) consume its words in
+ *                order; a uniform negative takes one word:
+ *                u = floor(word * (n-1) / 2^32), s = u + (u >= i) (weighted
+ *                samplers: see snap_sampler).
  *
  * Asynchronous: enqueues one kernel per epoch (HOGWILD modes) or 2 per chunk
  * (SYNC) and returns.  Errors: INVALID_ARG, CUDA, NUMERIC (from an earlier
