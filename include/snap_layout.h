@@ -60,8 +60,8 @@ typedef enum {
      * reshuffled every epoch; a lane keeps the current row's source in
      * registers and applies both directed steps (i, j) and (j, i) of every
      * entry, each with its own negatives.  Partners are written back with
-     * plain racy stores: concurrent writers may overwrite each other (the
-     * paper's description of its lock-free scheme). */
+     * racy writes (64-bit exchanges): concurrent writers may overwrite each
+     * other (the paper's description of its lock-free scheme). */
     SNAP_MODE_HOGWILD = 0,
     /* As HOGWILD, but every partner update is an atomic float add of the
      * change computed from a racy read (HOGWILD!'s component-wise atomic
@@ -120,7 +120,7 @@ typedef struct {
     int32_t flags;            /* SNAP_FLAG_* bits */
     float max_inflight;       /* HOGWILD modes: at most this share of the graph's entries in flight at
                                  once (lanes = share x entries); 0 = default (HOGWILD 0.01,
-                                 HOGWILD_RED 0.003).  Concurrent updates of one vertex degrade Hogwild
+                                 HOGWILD_RED 0.005).  Concurrent updates of one vertex degrade Hogwild
                                  quality on small graphs */
 } snap_options;
 

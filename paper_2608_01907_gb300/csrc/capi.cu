@@ -744,9 +744,10 @@ static snap_status check_schedule(const snap_schedule *s) {
 // of one vertex cost Hogwild quality; atomic adds of changes computed from
 // the same stale position overshoot where overwrites undershoot, so
 // HOGWILD_RED takes a lower share (LFR 260k / 6.9M, 5 seeds, NP against the
-// oracle: HOGWILD_RED -1.4% at 1%, -0.4% at 0.3% and at 0.1%; HOGWILD +0.5%
-// at 1%).  On the 34M-edge R-MAT graph both shares exceed the resident lanes.
-static double default_inflight(int red) { return red ? 0.003 : 0.01; }
+// oracle: HOGWILD_RED -1.4% at 1%, -0.7% at 0.5%, -0.4% at 0.3%; HOGWILD
+// +0.4% at 1%).  0.5% costs no time on LFR or R-MAT 2^20 (0.3%: 1.4-1.6x
+// slower); on the 34M-edge R-MAT graph every share exceeds the resident lanes.
+static double default_inflight(int red) { return red ? 0.005 : 0.01; }
 
 // Grid of a HOGWILD epoch: enough blocks for every segment, at most the
 // resident maximum, and at most max_inflight * entries lanes (one entry in

@@ -31,21 +31,19 @@ namespace snap {
 namespace {
 
 // Applies an update to a partner: racy write of the lane's value (HOGWILD)
-// or atomic add of the change (HOGWILD_RED).  HOT: the partner may be a
-// vertex that many lanes write at once (weighted negatives draw hubs in
-// proportion to their degree); L2 serialises plain stores to one address far
-// more than atomics, so the write is an atomic exchange -- the same
-// last-writer-wins result (R-MAT 2^22, degree negatives: 71 -> 8.5 ms per
-// epoch; with uniform negatives the plain store is 2% faster).
-template <bool RED, bool HOT = false>
+// or atomic add of the change (HOGWILD_RED).  The HOGWILD write is a 64-bit
+// atomic exchange -- the same last-writer-wins result as a store -- because
+// L2 serialises plain stores to an address that many lanes write at once far
+// more than atomics: vertices of high degree on power-law graphs, hubs drawn
+// by weighted negatives (epoch times with plain stores -> exchanges: LFR 260k
+// 2.41 -> 0.77 ms, R-MAT 2^20 2.06 -> 1.19 ms, R-MAT 2^22 4.92 -> 4.84 ms;
+// degree-weighted negatives on R-MAT 2^22 71 -> 9 ms).
+template <bool RED>
 __device__ __forceinline__ void apply_partner(float2 *pos, int32_t idx, float2 newv, float2 delta) {
-    if (RED) {
+    if (RED)
         atomicAdd(pos + idx, delta);
-    } else if (HOT) {
+    else
         exchange_pos(pos + idx, newv);
-    } else {
-        store_pos(pos + idx, newv);
-    }
 }
 
 // Energies of Table 1 / Eq. 2 for the actual energy of an epoch (Section
@@ -148,9 +146,8 @@ __device__ __forceinline__ GraphCtx graph_ctx(const OrientedArgs &a, int32_t row
 // Negatives of one group (up to 4, already gathered into v[]) for source
 // `src` held in ysrc; the vertex `other` is register-resident in yoth.
 // s[] and v[] are updated in place (v[m] = the value after its update).
-// E: add each pair's U^r at the moment of its update to en.  HOT: the
-// negatives are weighted draws (see apply_partner).
-template <bool RED, bool E, bool HOT>
+// E: add each pair's U^r at the moment of its update to en.
+template <bool RED, bool E>
 __device__ __forceinline__ void negative_group(float2 *pos, float eta, const int32_t (&s)[4], float2 (&v)[4], int nm,
                                                float2 &ysrc, int32_t other, float2 &yoth, float &en) {
 #pragma unroll
@@ -171,7 +168,7 @@ __device__ __forceinline__ void negative_group(float2 *pos, float eta, const int
             if (s[m] == other)
                 yoth = x;
             else
-                apply_partner<RED, HOT>(pos, s[m], x, make_float2(-dg.x, -dg.y));
+                apply_partner<RED>(pos, s[m], x, make_float2(-dg.x, -dg.y));
             v[m] = x;
         }
     }
@@ -200,7 +197,7 @@ __device__ __forceinline__ void later_negatives(const OrientedArgs &a, const Gra
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             if (m < nm) v[m] = load_pos(a.pos + s[m]);
-        negative_group<RED, E, W>(a.pos, c.eta, s, v, nm, ysrc, other, yoth, en);
+        negative_group<RED, E>(a.pos, c.eta, s, v, nm, ysrc, other, yoth, en);
     }
 }
 
@@ -247,7 +244,7 @@ __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, const Grap
         yi.y += df.y;
         yj.x -= df.x;
         yj.y -= df.y;
-        if (G > 0) negative_group<RED, E, W>(a.pos, eta, s1, v1, G, yi, j, yj, en);
+        if (G > 0) negative_group<RED, E>(a.pos, eta, s1, v1, G, yi, j, yj, en);
         if (a.k > 4) later_negatives<RED, W, E>(a, c, e1, i, yi, j, yj, wc1, en);
     }
     // direction 2: (j, i), source j
@@ -271,7 +268,7 @@ __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, const Grap
 #pragma unroll
                 for (int m = 0; m < G; ++m) v2[m] = load_pos(a.pos + s2[m]);
             }
-            negative_group<RED, E, W>(a.pos, eta, s2, v2, G, yj, i, yi, en);
+            negative_group<RED, E>(a.pos, eta, s2, v2, G, yj, i, yi, en);
         }
         if (a.k > 4) later_negatives<RED, W, E>(a, c, e2, j, yj, i, yi, wc2, en);
     }

@@ -107,9 +107,7 @@ __device__ __forceinline__ float2 repulsion_on_i(float dx, float dy) {
 
 // Position accesses that must see other SMs' writes: cached in L2 only.
 __device__ __forceinline__ float2 load_pos(const float2 *p) { return __ldcg(p); }
-__device__ __forceinline__ void store_pos(float2 *p, float2 v) { __stcg(p, v); }
-
-// The same write as one 64-bit atomic exchange (for addresses many lanes write).
+// A position written as one 64-bit atomic exchange (racy, last writer wins).
 __device__ __forceinline__ void exchange_pos(float2 *p, float2 v) {
     unsigned long long bits;
     memcpy(&bits, &v, 8);
