@@ -379,7 +379,8 @@ def run_snap(args, rank, world, local_rank):
     if not args.no_extras:
         from paper_2608_01907_gb300 import probe
         scratch = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
-        op = "load_dep_atomic" if mode == snap.MODE_HOGWILD_RED else "load_store"
+        # the write each mode issues after its read: an atomic add (HOGWILD_RED) or an exchange (HOGWILD)
+        op = "load_dep_atomic" if mode == snap.MODE_HOGWILD_RED else "load_exch"
         rmw_peak = max(probe.random_access_rate(scratch, op, depth=d, iters=32) for d in (1, 4))
         del scratch
 
