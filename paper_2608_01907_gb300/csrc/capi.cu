@@ -125,7 +125,7 @@ struct StatusSlots {
 StatusSlots g_status_slots;
 
 // SplitMix64 finaliser (Steele, Lea, Flood 2014): the per-epoch offset of
-// the segment order.
+// the slot-group order.
 uint64_t mix64(uint64_t x) {
     x += 0x9E3779B97F4A7C15ull;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -301,7 +301,7 @@ static int64_t golden_multiplier(int64_t m) {
 // (Re)cuts the oriented list into chunks of `target` entries: the entries
 // move from the current layout (row-major right after construction) into a
 // fresh array in the new slot order, and the slot table is rebuilt.
-static cudaError_t set_segments(snap_layout *h, AllocCounter &ac, int32_t target, cudaStream_t stream) {
+static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, cudaStream_t stream) {
     if (h->act_nnz > 0 && target > h->act_nnz) target = (int32_t)h->act_nnz;   // one chunk
     if (h->last_use) cudaStreamWaitEvent(stream, h->last_use, 0);   // the old arrays' last readers
     ChunkLayout to;
@@ -401,7 +401,7 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
                     (long long)h->act_nnz);
     h->act_layout = ChunkLayout{0, 0, 0, 0};   // row-major
     h->act_ent_bytes = 0;
-    err = set_segments(h, ac, h->act_seg_len, stream);
+    err = set_chunks(h, ac, h->act_seg_len, stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
     if (err != cudaSuccess) return cuda_fail(err, "oriented chunks");
     h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
@@ -545,7 +545,7 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     h->num_graphs = graph_offsets ? num_graphs : 1;
     if (graph_offsets && num_graphs > 1) h->graph_offsets.assign(graph_offsets, graph_offsets + num_graphs + 1);
     // CSR segments: the synchronous kernel's unit of work (and the
-    // validation pass); the HOGWILD modes use segments of oriented entries.
+    // validation pass); the HOGWILD modes use chunks of oriented entries.
     h->seg_len = (o.mode == SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 32;
     h->act_seg_len = (o.mode != SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 0;   // 0: by size
     h->block = o.block_threads ? o.block_threads : 256;
@@ -749,10 +749,10 @@ static snap_status check_schedule(const snap_schedule *s) {
 // slower); on the 34M-edge R-MAT graph every share exceeds the resident lanes.
 static double default_inflight(int red) { return red ? 0.005 : 0.01; }
 
-// Grid of a HOGWILD epoch: enough blocks for every segment, at most the
+// Grid of a HOGWILD epoch: enough blocks for every chunk, at most the
 // resident maximum, and at most max_inflight * entries lanes (one entry in
 // flight per lane), so small graphs are not updated by too many lanes at
-// once (each lane grid-strides over several segments instead).
+// once (each lane grid-strides over several chunks instead).
 static int inflight_grid(const snap_layout *h, int gmax) {
     const int64_t want = (h->act_num_segs + h->block - 1) / h->block;
     int64_t grid = want < gmax ? want : gmax;
@@ -835,7 +835,7 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
             if (h->act_num_segs == 0) continue;
             const int grid = inflight_grid(h, gmax);
             {
-                // lanes beyond the segment count are idle
+                // lanes beyond the chunk count are idle
                 const double lanes = (double)grid * h->block;
                 const double segs = (double)h->act_num_segs;
                 a.inflight_share = (float)((lanes < segs ? lanes : segs) / segs);
@@ -1073,7 +1073,7 @@ snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int3
             const int g = neg_samples < 4 ? neg_samples : 4;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
             (void)max_inflight;
-            if ((err = set_segments(h, ac, target, stream)) != cudaSuccess) break;
+            if ((err = set_chunks(h, ac, target, stream)) != cudaSuccess) break;
             h->block = block;
             h->grid_oriented[red][g] = 0;
             h->grid_oriented[red][g] =
@@ -1100,7 +1100,7 @@ snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int3
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err == cudaSuccess) {
-        err = set_segments(h, ac, best_t, stream);
+        err = set_chunks(h, ac, best_t, stream);
         h->block = best_b;
         for (auto &row : h->grid_oriented)
             for (int &v : row) v = 0;
