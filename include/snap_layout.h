@@ -259,19 +259,44 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
 
 /*
  * snap_layout_autotune -- choose the chunk size (oriented entries per lane)
- * and the block size of a HOGWILD handle by timing epochs.  Candidates are
- * 4, 8, 16, 32 entries x 128/256 threads, all under the handle's
- * max_inflight bound (max_inflight here is unused and kept for the ABI).  The
- * chosen configuration stays on the handle.
+ * and the block size of a HOGWILD handle: the fastest configuration whose
+ * layout quality stays within `tolerance` of the configuration the handle
+ * has on entry.  The choice stays on the handle.
  *
- *   scratch_positions  device, n x 2 float32; overwritten (3 epochs per
- *                      candidate at a constant step).
- *   chosen_segment, chosen_block, chosen_ms   host outputs (nullable).
- * Synchronises the stream.  Errors: INVALID_ARG, NOT_SUPPORTED (SYNC), CUDA.
+ * Candidates: the entry configuration and 4, 8, 16, 32 entries x 128/256
+ * threads.  Longer chunks apply more of one source's steps back to back,
+ * which is faster but moves the visiting order away from Algorithm 1's
+ * shuffled order and can cost energy (Section 3.4's lock-free scheme
+ * bounds concurrency, not order).
+ *   1. Timing: each candidate runs the schedule's epoch 0 untimed and epochs
+ *      1-3 timed (CUDA events) on scratch_positions, in two passes over the
+ *      candidates; the faster pass counts.  A candidate stays in the running
+ *      only if it is at least 3% faster than the entry configuration.
+ *   2. Quality gate (tolerance >= 0): candidates in increasing time are laid
+ *      out from initial_positions for schedule->total_epochs epochs with
+ *      `seed`, and the first whose Eq. 4 objective U satisfies
+ *      U <= (1 + tolerance) U_entry is chosen (U_entry: the entry
+ *      configuration's layout; the objective is exact for batches and
+ *      n <= 16384, otherwise the same 2^24 sampled pairs for every
+ *      candidate).  A candidate whose layout becomes non-finite is
+ *      rejected.  The entry configuration always passes.
+ *      tolerance < 0: no gate, the fastest remaining candidate is chosen.
+ *
+ *   initial_positions  device, n x 2 float32, read only (may be NULL when
+ *                      tolerance < 0).
+ *   scratch_positions  device, n x 2 float32; overwritten.
+ *   neg_samples, schedule, seed   as for snap_layout_epochs.
+ *   chosen_segment, chosen_block, chosen_ms (ms per epoch),
+ *   chosen_objective (U of the chosen layout; NaN without the gate)
+ *                      host outputs, nullable.
+ * Synchronises the stream.  Errors: INVALID_ARG, NOT_SUPPORTED (SYNC),
+ * NUMERIC (the entry configuration's layout became non-finite), CUDA.  On
+ * an error the handle keeps a valid configuration.
  */
-snap_status snap_layout_autotune(snap_layout_t h, float *scratch_positions, int32_t neg_samples,
-                                 double max_inflight, int32_t *chosen_segment, int32_t *chosen_block,
-                                 double *chosen_ms, void *cuda_stream);
+snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions, float *scratch_positions,
+                                 int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
+                                 double tolerance, int32_t *chosen_segment, int32_t *chosen_block,
+                                 double *chosen_ms, double *chosen_objective, void *cuda_stream);
 
 /* Release the handle and its device memory.  NULL is ignored.  Does not
  * synchronise: the memory is freed stream-ordered after the work of the

@@ -95,7 +95,7 @@ def load_library():
     lib.snap_layout_objective.restype = st
     lib.snap_layout_check.argtypes = [P, P]
     lib.snap_layout_check.restype = st
-    lib.snap_layout_autotune.argtypes = [P, P, i32, f64, P, P, P, P]
+    lib.snap_layout_autotune.argtypes = [P, P, P, i32, P, u64, f64, P, P, P, P, P]
     lib.snap_layout_autotune.restype = st
     lib.snap_layout_device_bytes.argtypes = [P]
     lib.snap_layout_device_bytes.restype = i64
@@ -242,13 +242,19 @@ def snap_layout_check(h, stream=None) -> None:
     _check(load_library().snap_layout_check(h, _stream(stream)))
 
 
-def snap_layout_autotune(h, scratch_positions, neg_samples: int, max_inflight: float = 0.0, stream=None):
-    """Returns (segment entries, block threads, ms per epoch) chosen for the handle."""
-    seg, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(load_library().snap_layout_autotune(h, _device_positions(scratch_positions), neg_samples, max_inflight,
-                                               ctypes.byref(seg), ctypes.byref(blk), ctypes.byref(ms),
+def snap_layout_autotune(h, scratch_positions, neg_samples: int, schedule: SnapSchedule, seed: int,
+                         initial_positions=None, tolerance: float = 0.02, stream=None):
+    """Returns (chunk entries, block threads, ms per epoch, objective) chosen for the
+    handle; tolerance < 0 (or no initial positions) times the candidates only."""
+    if initial_positions is None:
+        tolerance = -1.0
+    seg, blk, ms, u = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    init = _device_positions(initial_positions) if initial_positions is not None else None
+    _check(load_library().snap_layout_autotune(h, init, _device_positions(scratch_positions), neg_samples,
+                                               ctypes.byref(schedule), seed, tolerance, ctypes.byref(seg),
+                                               ctypes.byref(blk), ctypes.byref(ms), ctypes.byref(u),
                                                _stream(stream)))
-    return seg.value, blk.value, ms.value
+    return seg.value, blk.value, ms.value, u.value
 
 
 def snap_layout_device_bytes(h) -> int:
@@ -419,6 +425,13 @@ class Layout:
     def objective(self, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0, seed: int = 0):
         _device_positions(positions, self.n)
         return snap_layout_objective(self.handle, positions, neg_samples, exact, pair_samples, seed, self.stream)
+
+    def autotune(self, initial_positions, scratch_positions, neg_samples: int, schedule: SnapSchedule, seed: int,
+                 tolerance: float = 0.02):
+        _device_positions(initial_positions, self.n)
+        _device_positions(scratch_positions, self.n)
+        return snap_layout_autotune(self.handle, scratch_positions, neg_samples, schedule, seed, initial_positions,
+                                    tolerance, self.stream)
 
     def check(self) -> None:
         snap_layout_check(self.handle, self.stream)

@@ -129,16 +129,81 @@ def test_autotune_picks_a_bounded_configuration(cuda):
     torch = cuda
     from synth import tiny_graph
     g = tiny_graph(60_000, 500_000, seed=9)
+    sched = snap.linear_schedule(1.0, 10)
     scratch = torch.from_numpy(initial_positions(g.n, 1)).cuda()
     with snap.Layout(g.row_ptr, g.col_idx) as L:
-        seg, blk, ms = snap.snap_layout_autotune(L.handle, scratch, 3, 1.0 / 64)
-        assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0
+        seg, blk, ms, u = snap.snap_layout_autotune(L.handle, scratch, 3, sched, 7)   # timing only
+        assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0 and np.isnan(u)
         pos = torch.from_numpy(initial_positions(g.n, 2)).cuda()
         before = L.objective(pos, 3)[2]
-        L.epochs(pos, 0, 10, 3, snap.linear_schedule(1.0, 10), 3)
+        L.epochs(pos, 0, 10, 3, sched, 3)
         L.check()
         assert L.objective(pos, 3)[2] < before
     with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(mode=snap.MODE_SYNC)) as L:
         with pytest.raises(snap.SnapError) as ei:
-            snap.snap_layout_autotune(L.handle, scratch, 3)
+            snap.snap_layout_autotune(L.handle, scratch, 3, sched, 7)
         assert ei.value.status == 5
+
+
+@pytest.mark.parametrize("mode", [snap.MODE_HOGWILD_RED, snap.MODE_HOGWILD])
+def test_autotune_quality_gate(cuda, mode):
+    """The chosen configuration's layout is within the tolerance of the entry
+    configuration's (same initial positions, schedule and seed), and reproduces
+    the objective the autotuner reports when laid out again."""
+    torch = cuda
+    from synth import tiny_graph
+    g = tiny_graph(60_000, 500_000, seed=9)
+    sched = snap.linear_schedule(1.0, 10)
+    init = torch.from_numpy(initial_positions(g.n, 4)).cuda()
+    scratch = torch.empty_like(init)
+    opts = snap.make_options(mode=mode)
+    with snap.Layout(g.row_ptr, g.col_idx, opts=opts) as L:
+        pos = init.clone()
+        L.epochs(pos, 0, 10, 3, sched, 5)
+        L.check()
+        u_entry = L.objective(pos, 3, exact=False, pair_samples=1 << 24, seed=5 ^ 0x5bd1e9955bd1e995)[2]
+        seg, blk, ms, u = L.autotune(init, scratch, 3, sched, 5, tolerance=0.02)
+        assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0
+        # the gate compares against its own run of the entry configuration;
+        # u_entry is another run of it (Hogwild runs differ by well under 1%)
+        assert np.isfinite(u) and u <= u_entry * 1.03
+        pos = init.clone()
+        L.epochs(pos, 0, 10, 3, sched, 5)
+        L.check()
+        again = L.objective(pos, 3, exact=False, pair_samples=1 << 24, seed=5 ^ 0x5bd1e9955bd1e995)[2]
+        assert again == pytest.approx(u, rel=0.02)
+    with snap.Layout(g.row_ptr, g.col_idx, opts=opts) as L:
+        seg0, blk0, _, u0 = L.autotune(init, scratch, 3, sched, 5, tolerance=0.0)
+        assert seg0 in (4, 8, 16, 32) and blk0 in (128, 256)
+        assert np.isfinite(u0) and u0 <= u_entry * 1.01
+
+
+def test_autotune_on_a_batch_with_a_captured_epoch_loop(cuda):
+    """The autotuner on a batch handle (exact per-graph objective in the gate),
+    then the 30-epoch loop captured as a CUDA graph: the captured layout
+    reaches the objective the gate measured, and so does its replay."""
+    torch = cuda
+    graphs = _graphs(64, seed=11, nmax=4000)
+    Y0 = _batch_positions(graphs, 9)
+    rp, ci, offs = snap.batch_union([(g.row_ptr, g.col_idx) for g in graphs])
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=30)
+    init = torch.from_numpy(Y0).cuda()
+    scratch = torch.empty_like(init)
+    pos = torch.empty_like(init)
+    h = snap.snap_layout_create_batch(rp, ci, offs, snap.make_options(cuda_graph=True))
+    try:
+        seg, blk, ms, u = snap.snap_layout_autotune(h, scratch, 3, sched, 2, init, 0.02)
+        assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0 and np.isfinite(u)
+        pos.copy_(init)
+        before = snap.snap_layout_objective(h, pos, 3, True)[2]
+        snap.snap_layout_epochs(h, pos, 0, 30, 3, sched, 2)     # captured, then launched
+        snap.snap_layout_check(h)
+        after = snap.snap_layout_objective(h, pos, 3, True)[2]
+        assert after < before
+        assert after == pytest.approx(u, rel=0.02)
+        pos.copy_(init)
+        snap.snap_layout_epochs(h, pos, 0, 30, 3, sched, 2)     # replayed
+        snap.snap_layout_check(h)
+        assert snap.snap_layout_objective(h, pos, 3, True)[2] == pytest.approx(after, rel=0.02)
+    finally:
+        snap.snap_layout_destroy(h)
