@@ -388,15 +388,14 @@ def run_snap(args, rank, world, local_rank):
     deg = np.diff(row_ptr)
     nonempty = int((deg > 0).sum())
     alg_bytes = nnz * (4 + 16 * (1 + k)) + 8 * (n + 1) + 16 * nonempty
-    avg_launch_s = float(np.mean(launch_ms)) / 1e3 / (launches_per_epoch if mode == snap.MODE_SYNC else 1)
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (float(np.mean(launch_ms)) / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": recorded_traffic(args.mode, k),
-            "kernel": "hogwild_epoch_kernel" if mode != snap.MODE_SYNC else "sync epoch (chunk+apply)",
+            "kernel": (f"oriented_epoch_kernel<RED={int(mode == snap.MODE_HOGWILD_RED)},G={min(k, 4)}>"
+                       if mode != snap.MODE_SYNC else "sync epoch (sync_chunk_kernel + sync_apply_kernel)"),
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": float(np.mean(launch_ms)),
             "peak_source": f"{peak_kind} hbm_gbs (copy)"}
-    del avg_launch_s
     roof_l2 = None
     if rmw_peak and mode != snap.MODE_SYNC:
         # per undirected edge the oriented kernel read-modify-writes the
