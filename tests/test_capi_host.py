@@ -115,6 +115,9 @@ def test_null_handle_errors(lib):
     sched = snap.linear_schedule()
     assert lib.snap_layout_epochs(None, P(8), 0, 1, 3, ctypes.byref(sched), 1, None) == 1
     assert b"NULL" in lib.snap_last_error()
+    assert lib.snap_layout_autotune(None, P(8), P(8), 3, ctypes.byref(sched), 1, 0.02, None, None, None, None,
+                                    None) == 1
+    assert b"NULL" in lib.snap_last_error()
 
 
 def _edge_set(rp, ci):
