@@ -599,8 +599,6 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     h->h_status = g_status_slots.take();
     SNAP_CUDA(h->h_status ? cudaSuccess : cudaErrorMemoryAllocation, "pinned status word");
     SNAP_CUDA(cudaEventCreateWithFlags(&h->status_event, cudaEventDisableTiming), "status event");
-    std::vector<int32_t> deg((size_t)n);
-    for (int32_t i = 0; i < n; ++i) deg[(size_t)i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
     SNAP_CUDA(cudaMemcpyAsync(h->d_row_ptr, row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice,
                               stream), "copy row_ptr");
     if (h->nnz > 0)
@@ -608,8 +606,7 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
                                   stream), "copy col_idx");
     SNAP_CUDA(cudaMemsetAsync(h->d_col + h->nnz, 0, sizeof(int32_t) * (col_entries - (size_t)h->nnz), stream),
               "clear col_idx padding");
-    SNAP_CUDA(cudaMemcpyAsync(h->d_deg, deg.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, stream),
-              "copy degrees");
+    SNAP_CUDA(launch_degrees(h->d_row_ptr, n, h->d_deg, stream), "degree kernel");
     SNAP_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t) * 4, stream), "clear status");
     std::vector<int32_t> node_graph;
     if (h->num_graphs > 1) {

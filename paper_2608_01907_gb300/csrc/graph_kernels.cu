@@ -31,6 +31,13 @@ __global__ void segment_rows_kernel(const int64_t *__restrict__ row_ptr, int32_t
     }
 }
 
+// deg[i] = row_ptr[i+1] - row_ptr[i] (row_ptr checked non-decreasing on the host).
+__global__ void degrees_kernel(const int64_t *__restrict__ row_ptr, int32_t n, int32_t *__restrict__ deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        deg[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
+}
+
 __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                     const int32_t *__restrict__ seg_row, int32_t n, int64_t nnz,
                                     int32_t seg_len, uint32_t *flags_out, const int32_t *__restrict__ node_graph) {
@@ -425,6 +432,14 @@ cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, 
     const int grid = (int)(want < 65536 ? want : 65536);
     segment_rows_kernel<<<grid, block, 0, s>>>(row_ptr, n, seg_len, seg_row, num_segs);
     (void)nnz;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degrees(const int64_t *row_ptr, int32_t n, int32_t *deg, cudaStream_t s) {
+    const int block = 256;
+    const int64_t want = ((int64_t)n + block - 1) / block;
+    const int grid = (int)(want < 65536 ? (want > 0 ? want : 1) : 65536);
+    degrees_kernel<<<grid, block, 0, s>>>(row_ptr, n, deg);
     return cudaGetLastError();
 }
 

@@ -178,6 +178,7 @@ cudaError_t launch_sync_apply(float2 *pos, long long *disp, int32_t n, float eta
                               int32_t tick = 0, float cap = 0.0f);
 int sync_blocks_per_sm(int block);
 
+cudaError_t launch_degrees(const int64_t *row_ptr, int32_t n, int32_t *deg, cudaStream_t s);
 cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, int32_t seg_len,
                                 int32_t *seg_row, int64_t num_segs, cudaStream_t s);
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
