@@ -440,8 +440,11 @@ def run_snap(args, rank, world, local_rank):
 
     l2_bytes = getattr(torch.cuda.get_device_properties(local_rank), "L2_cache_size", 126 << 20)
     pos_mb, stream_mb = 8 * n / 1e6, 16 * (nnz // 2) / 1e6
-    l2_note = (f"inputs larger than L2 ({l2_bytes / 1e6:.0f} MB): the {stream_mb:.0f} MB entry stream is re-read "
-               f"every epoch; the {pos_mb:.1f} MB positions "
+    l2_note = ((f"inputs larger than L2 ({l2_bytes / 1e6:.0f} MB): the {stream_mb:.0f} MB entry stream is re-read "
+                if stream_mb * 1e6 > l2_bytes else
+                f"inputs smaller than L2 ({l2_bytes / 1e6:.0f} MB) and not flushed: the {stream_mb:.0f} MB entry "
+                f"stream is re-read ")
+               + f"every epoch; the {pos_mb:.1f} MB positions "
                + ("stay L2-resident by design" if 8 * n < l2_bytes // 2 else "exceed L2 (random gathers reach HBM)"))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
