@@ -653,8 +653,8 @@ def run_serve(args, rank, world, local_rank):
                        "jobs": len(arrivals), "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
                        "graph_pool": "48 graphs: R-MAT / 8-community planted partition, |E| log-uniform 1k-2M",
                        "mode": "hogwild_red",
-                       "l2": "not flushed: each job's entries (<= 32 MB) and positions may stay in L2 across its "
-                             "epochs, as they would in any server; the admitted jobs together exceed L2"},
+                       "l2": "not flushed: a job's entries (<= 32 MB) and positions may stay in L2 across its "
+                             "epochs, as they would in any server"},
             "continuous_batching": srv, "one_job_at_a_time": seq,
             "p99_speedup": seq["p99_s"] / srv["p99_s"], "throughput_ratio": srv["updates_per_s"] / seq["updates_per_s"],
             "all_finite": finite, "clocks": clk}
