@@ -380,3 +380,43 @@ def test_np_is_one_for_a_lattice_grid_embedding():
     assert oracle.neighborhood_preservation(rp, ci, side * side, rng.permutation(Y)) < 0.3
     sample = np.array([0, 11, 55, 99], dtype=np.int32)
     assert oracle.neighborhood_preservation(rp, ci, side * side, Y, sample) == 1.0
+
+
+# --------------------------------------------------------------------------
+# Sparsity of the updates (Section 3.4): one update is a directed step with its
+# k negatives; a vertex v takes part in the 2 d_v steps it is an endpoint of
+# and in about 2|E| k / (|V|-1) draws, so the largest share of updates that
+# touch one vertex is Delta ~ d_max/|E| + k/(|V|-1), and two random updates
+# share a vertex with probability rho <= (k+2) Delta.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("gen", ["sbm", "rmat"])
+def test_update_sparsity_of_section_3_4(gen):
+    from synth import rmat_graph
+    g = sbm_graph(seed=1) if gen == "sbm" else rmat_graph(12, 30_000, seed=3)
+    n, rp, ci = g.n, g.row_ptr, g.col_idx
+    nnz = int(rp[-1])
+    E, k = nnz // 2, 3
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    touch = np.zeros(n, dtype=np.int64)
+    sets = []
+    for e in range(nnz):
+        s, _ = oracle.edge_negatives(e, 0, 7, int(rows[e]), n, k)
+        vs = {int(rows[e]), int(ci[e]), *s.tolist()}
+        for v in vs:
+            touch[v] += 1
+        sets.append(vs)
+    dmax = int(np.diff(rp).max())
+    delta_paper = dmax / E + k / (n - 1)
+    delta = touch.max() / nnz
+    # the endpoint term is exact; the draws of the busiest vertex exceed their
+    # mean 2|E| k/(|V|-1) by a few binomial standard deviations at most
+    mean_draws = nnz * k / (n - 1)
+    assert dmax / E <= delta <= delta_paper + 6 * math.sqrt(mean_draws) / nnz
+    rng = np.random.default_rng(5)
+    m = 200_000
+    a, b = rng.integers(0, nnz, m), rng.integers(0, nnz, m)
+    hits = sum(1 for x, y in zip(a.tolist(), b.tolist()) if x != y and sets[x] & sets[y])
+    rho = hits / m
+    assert rho <= (k + 2) * delta_paper
+    # and the bound is not vacuous: conflicts do happen at this size
+    assert rho > 0.05 * (k + 2) * delta_paper
