@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI declared in include/snap_layout.h: handle life cycle,
 // argument checking, launch configuration and error reporting.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -54,6 +55,15 @@ struct AllocCounter {
 };
 
 thread_local AllocCounter g_alloc;
+
+// NVTX range over one library call (host timeline; a no-op unless a
+// profiler that collects NVTX is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 thread_local bool g_in_run = false;
 
 // Handle memory is stream-ordered (cudaMallocAsync on the creating stream,
@@ -507,6 +517,7 @@ static snap_status sampler_tables(const snap_options &o, const int64_t *row_ptr,
 static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *degrees, int32_t n,
                                const int32_t *graph_offsets, int32_t num_graphs, const snap_options *opts,
                                void *cuda_stream, snap_layout_t *out) {
+    NvtxRange nvtx_range("snap_layout_create");
     if (!out) return fail(SNAP_ERR_INVALID_ARG, "out is NULL");
     snap_status st = check_csr_host(row_ptr, col_idx, degrees, n);
     if (st != SNAP_OK) return st;
@@ -769,6 +780,7 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
     const snap_schedule *schedule = &sched;
     cudaError_t err = cudaSuccess;
     for (int32_t ep = 0; ep < epochs; ++ep) {
+        NvtxRange nvtx_epoch("epoch");
         const int32_t t = epoch_begin + ep;
         const double eta = step_size(*schedule, t);
         if (h->opts.mode == SNAP_MODE_SYNC) {
@@ -883,6 +895,7 @@ static cudaError_t set_batch_schedule(snap_layout *h, const snap_schedule &sc, u
 static snap_status epochs_impl(snap_layout_t h, float *positions, int32_t epoch_begin, int32_t epochs,
                                int32_t neg_samples, const snap_schedule *schedule, uint64_t seed, double *energy,
                                void *cuda_stream) {
+    NvtxRange nvtx_range("snap_layout_epochs");
     if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
     if (!positions) return fail(SNAP_ERR_INVALID_ARG, "positions is NULL");
     if (((uintptr_t)positions & 7u) != 0) return fail(SNAP_ERR_INVALID_ARG, "positions must be 8-byte aligned");
@@ -1048,6 +1061,7 @@ static snap_status objective_impl(snap_layout *h, const float2 *pos, int32_t neg
 snap_status snap_layout_objective(snap_layout_t h, const float *positions, int32_t neg_samples, int32_t exact,
                                   int64_t pair_samples, uint64_t seed, double *out_attr, double *out_rep,
                                   double *out_total, void *cuda_stream) {
+    NvtxRange nvtx_range("snap_layout_objective");
     if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
     if (!positions) return fail(SNAP_ERR_INVALID_ARG, "positions is NULL");
     if (((uintptr_t)positions & 7u) != 0) return fail(SNAP_ERR_INVALID_ARG, "positions must be 8-byte aligned");
@@ -1096,6 +1110,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
                                  int32_t neg_samples, const snap_schedule *schedule, uint64_t seed, double tolerance,
                                  int32_t *chosen_segment, int32_t *chosen_block, double *chosen_ms,
                                  double *chosen_objective, void *cuda_stream) {
+    NvtxRange nvtx_range("snap_layout_autotune");
     if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
     if (h->opts.mode == SNAP_MODE_SYNC) return fail(SNAP_ERR_NOT_SUPPORTED, "autotuning applies to the HOGWILD modes");
     if (!scratch_positions || ((uintptr_t)scratch_positions & 7u) != 0)
@@ -1238,6 +1253,7 @@ void snap_layout_destroy(snap_layout_t h) {
 snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, const snap_options *opts,
                             float *positions_host, int32_t epochs, int32_t neg_samples, const snap_schedule *schedule,
                             uint64_t seed, void *cuda_stream) {
+    NvtxRange nvtx_range("snap_layout_run");
     if (!positions_host) return fail(SNAP_ERR_INVALID_ARG, "positions_host is NULL");
     snap_status st = check_schedule(schedule);
     if (st != SNAP_OK) return st;
@@ -1335,6 +1351,7 @@ snap_status snap_multi_create(int32_t max_jobs, snap_multi_t *out) {
 snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float *const *positions,
                              const int32_t *epochs, const snap_schedule *schedules, const uint64_t *seeds,
                              int32_t count, int32_t neg_samples, void *cuda_stream) {
+    NvtxRange nvtx_range("snap_multi_epoch");
     if (!m || !handles || !positions || !epochs || !schedules || !seeds)
         return fail(SNAP_ERR_INVALID_ARG, "NULL argument");
     if (count < 0 || count > m->capacity) return fail(SNAP_ERR_INVALID_ARG, "count = %d out of [0, %d]", count,
