@@ -12,7 +12,10 @@ the server:
      returned to the budget once the copy has completed.
 A job that arrives while others are on the GPU therefore starts at the next
 tick, and small jobs are not stuck behind large ones.  Per-job latency is
-measured from submission to the moment its result is on the host.
+measured from submission to the moment its result is on the host.  A job can
+be cancelled while it waits or runs (cancel): it leaves the next tick's
+launch, its positions are not copied back, and its memory returns to the
+budget once the work already queued for it has completed.
 """
 from __future__ import annotations
 
@@ -48,6 +51,7 @@ class Job:
     pos_host: object = None
     done_event: object = None
     reserved: int = 0
+    cancelled: bool = False
     meta: dict = field(default_factory=dict)
 
     @property
@@ -79,6 +83,7 @@ class LayoutServer:
         self.active: list[Job] = []
         self.retiring: list[Job] = []
         self.done: list[Job] = []
+        self.cancelled: list[Job] = []
         self.used = 0
         self.ticks = 0
         self.updates = 0
@@ -90,6 +95,26 @@ class LayoutServer:
         if need > self.budget:
             raise ValueError(f"job {job.job_id} needs {need} bytes, more than the whole budget")
         self.waiting.append(job)
+
+    def cancel(self, job_id: int) -> bool:
+        """Withdraws a waiting or running job; False if it is unknown or its
+        result is already being copied back."""
+        for job in self.waiting:
+            if job.job_id == job_id:
+                self.waiting.remove(job)
+                job.cancelled = True
+                job.finished = self.clock()
+                self.cancelled.append(job)
+                return True
+        for job in self.active:
+            if job.job_id == job_id:
+                self.active.remove(job)
+                job.cancelled = True
+                job.done_event = self.torch.cuda.Event()
+                job.done_event.record(self.stream)     # after the last tick that used the job
+                self.retiring.append(job)
+                return True
+        return False
 
     def idle(self) -> bool:
         return not (self.waiting or self.active or self.retiring)
@@ -130,14 +155,15 @@ class LayoutServer:
         left = []
         for job in self.retiring:
             if job.done_event.query():
-                job.positions[:] = job.pos_host.numpy()
+                if not job.cancelled:
+                    job.positions[:] = job.pos_host.numpy()
                 job.finished = self.clock()
                 snap_layout_destroy(job.handle)
                 job.handle = None
                 job.pos_dev = None
                 job.pos_host = None
                 self.used -= job.reserved
-                self.done.append(job)
+                (self.cancelled if job.cancelled else self.done).append(job)
             else:
                 left.append(job)
         self.retiring = left

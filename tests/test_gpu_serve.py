@@ -70,6 +70,42 @@ def test_server_result_same_alone_and_in_the_mix_bitwise(cuda):
         assert job.submitted <= job.admitted <= job.finished
 
 
+def test_cancelled_jobs_leave_the_others_unchanged(cuda):
+    """One job is cancelled while it waits, one while it runs: the others'
+    results stay bitwise what they are alone, the cancelled jobs' positions
+    are not touched, and the whole budget comes back."""
+    torch = cuda
+    graphs = [tiny_graph(200 + 50 * q, 700, seed=20 + q) for q in range(6)]
+    server = LayoutServer(hbm_budget=1 << 30, max_jobs=2, epochs=12, neg_samples=3, eta0=0.8,
+                          segment_edges=ONE_LANE)
+    Y0 = [initial_positions(g.n, 30 + q) for q, g in enumerate(graphs)]
+    jobs = [Job(q, g.row_ptr, g.col_idx, Y0[q].copy(), seed=50 + q) for q, g in enumerate(graphs)]
+    try:
+        for job in jobs:
+            server.submit(job)
+        for _ in range(3):
+            server.tick()
+        assert [j.job_id for j in server.active] == [0, 1]
+        assert server.cancel(4)                 # still waiting (two slots)
+        assert server.cancel(1)                 # running, epoch 3 of 12
+        assert not server.cancel(99)
+        server.drain()
+        assert not server.cancel(0)             # finished
+    finally:
+        server.close()
+    assert sorted(j.job_id for j in server.done) == [0, 2, 3, 5]
+    assert sorted(j.job_id for j in server.cancelled) == [1, 4]
+    assert server.used == 0
+    sched = snap.linear_schedule(0.8, 12)
+    for job in jobs:
+        q = job.job_id
+        if job.cancelled:
+            assert np.array_equal(job.positions, Y0[q])
+            continue
+        alone = _alone(torch, graphs[q], Y0[q], 12, 3, sched, 50 + q, seg=ONE_LANE)
+        assert np.array_equal(job.positions.view(np.uint32), alone.view(np.uint32)), q
+
+
 def test_server_quality_in_the_mix_matches_alone(cuda):
     torch = cuda
     graphs = [sbm_graph(seed=s) for s in (1, 2, 3)] + [tiny_graph(20_000, 120_000, seed=4)]
