@@ -46,7 +46,7 @@ typedef enum {
     SNAP_ERR_INVALID_ARG = 1,    /* malformed CSR, bad size, null pointer, misaligned buffer */
     SNAP_ERR_OUT_OF_MEMORY = 2,  /* a device or host allocation failed; nothing leaked */
     SNAP_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed */
-    SNAP_ERR_TIMEOUT = 4,        /* a bounded device wait gave up */
+    SNAP_ERR_TIMEOUT = 4,        /* reserved: no kernel of this library waits on a flag */
     SNAP_ERR_NOT_SUPPORTED = 5,  /* the option or call is not supported for this handle */
     SNAP_ERR_NUMERIC = 6         /* a kernel met a non-finite or out-of-range value */
 } snap_status;
