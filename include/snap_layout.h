@@ -232,7 +232,7 @@ snap_status snap_layout_epochs_energy(snap_layout_t h, float *positions, int32_t
  * snap_layout_objective -- the energy the method descends (Eq. 4 with the
  * weight realised by uniform sampling, Section 3.3):
  *   U = sum_{(i,j) in E, i<j} U^a(r_ij) + k * sum_{i<j} w_ij U^r(r_ij),
- *   w_ij = (d_i + d_j) / (2(n-1)),
+ *   w_ij = (d_i + d_j) / (2(n-1))   (DEGREE / WEIGHTS samplers: the w_ij of snap_sampler),
  *   U^a(r) = alpha (r^2/2 + (beta/2) ln(1+r^2)),  U^r(r) = 1 / (2(1+r^2))
  * (the energies whose negative gradients are the Table 1 forces, Eq. 2).
  *
