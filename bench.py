@@ -529,6 +529,29 @@ def run_batch(args, rank, world, local_rank):
     updates = EPOCHS * nnz * (1 + k)
     snap.snap_layout_destroy(h)
 
+    # rooflines of one epoch launch, as for the single graph: algorithmic
+    # bytes against the HBM copy peak, and the launch's dependent random
+    # read + atomic adds against the probe's ceiling on an array of n slots
+    deg = np.diff(rp)
+    alg_bytes = nnz * (4 + 16 * (1 + k)) + 8 * (n + 1) + 16 * int((deg > 0).sum())
+    launch_s = ms / 1e3 / EPOCHS
+    peak, peak_kind = measured_peak()
+    roof = {"bound": "hbm", "achieved": alg_bytes / launch_s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg_bytes / launch_s / 1e9 / peak, "traffic": None,
+            "kernel": f"oriented_epoch_kernel<RED=1,G={min(k, 4)},MULTI=1>",
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_s * 1e3,
+            "launch_time": "30-epoch CUDA-graph replay (CUDA events on the stream) / 30",
+            "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    from paper_2608_01907_gb300 import probe
+    scratch = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    rmw_peak = max(probe.random_access_rate(scratch, "load_dep_atomic", depth=d, iters=32) for d in (1, 4))
+    del scratch
+    rmw_per_launch = (nnz // 2) * (1 + 2 * k)
+    roof_l2 = {"bound": "l2 dependent read-modify-write (random 8-byte slots)",
+               "achieved": rmw_per_launch / launch_s / 1e9, "peak": rmw_peak / 1e9, "unit": "G RMW/s",
+               "frac": rmw_per_launch / launch_s / rmw_peak, "rmw_per_launch": rmw_per_launch,
+               "peak_source": "probe kernel (csrc/probe_l2.cu) measured in this run on n float2 slots"}
+
     # one graph per handle and per launch, on a seeded sample of the graphs
     rng = np.random.default_rng(args.seed)
     sample = np.sort(rng.choice(offs.size - 1, min(args.per_graph_sample, offs.size - 1), replace=False))
@@ -567,6 +590,7 @@ def run_batch(args, rank, world, local_rank):
             "one_graph_per_launch": {"updates_per_s": upd_pg / (ms_pg / 1e3), "graphs_timed": len(handles),
                                      "launches": len(handles) * EPOCHS, "ms": ms_pg},
             "speedup_vs_one_graph_per_launch": (updates / (ms / 1e3)) / (upd_pg / (ms_pg / 1e3)),
+            "roofline": roof, "roofline_l2": roof_l2,
             "gpu_launches": args.steps * EPOCHS, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
