@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (MODE_HOGWILD_RED, MultiEpoch, SnapSchedule, linear_schedule, make_options, snap_layout_create,
-               snap_layout_destroy, snap_layout_device_bytes)
+               snap_layout_destroy)
 
 
 def estimated_bytes(n: int, nnz: int) -> int:

@@ -6,7 +6,7 @@ import pytest
 import oracle
 import paper_2608_01907_gb300 as snap
 from gpu_helpers import gpu_layout, schedule_dict
-from synth import Graph, batch_sbm_graphs, edges_to_csr, initial_positions
+from synth import batch_sbm_graphs, edges_to_csr, initial_positions
 
 pytestmark = pytest.mark.gpu
 

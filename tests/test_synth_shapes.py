@@ -3,7 +3,6 @@ for: each returns a valid symmetric CSR (rows strictly ascending, no loops)
 with the sizes, densities, degree skew and community mixing its recipe
 states.  Nothing here touches the method's arithmetic."""
 import numpy as np
-import pytest
 
 from synth import (batch_sbm_graphs, initial_positions, lfr_graph, rmat_graph, sbm_graph,
                    serving_graph_pool)
