@@ -420,3 +420,30 @@ def test_update_sparsity_of_section_3_4(gen):
     assert rho <= (k + 2) * delta_paper
     # and the bound is not vacuous: conflicts do happen at this size
     assert rho > 0.05 * (k + 2) * delta_paper
+
+
+# --------------------------------------------------------------------------
+# Fig. 3b: the stochastic epochs and the full computation optimise the same
+# energy.  Full-gradient descent on Eq. 4 (Y <- Y - eta_t 2 grad U, the
+# expected epoch displacement of Section 3.3, eta0 = 0.25: the largest of
+# 1 / 0.5 / 0.25 that stays stable on this graph) and Algorithm 1 (eta0 = 1)
+# from the same start reach the same objective and neighbourhood
+# preservation; the cluster placement may differ (another local minimum).
+# --------------------------------------------------------------------------
+def test_algorithm1_reaches_the_objective_of_full_gradient_descent():
+    g = sbm_graph(seed=1)
+    n, rp, ci, k, T = g.n, g.row_ptr, g.col_idx, 3, 30
+    Y0 = initial_positions(n, 1).astype(np.float64)
+    Y = Y0.copy()
+    for t in range(T):
+        eta = max(0.25 * (1 - t / T), 0.25e-3)
+        Y = Y - eta * 2 * oracle.exact_gradient(rp, ci, n, Y, k)
+    S = oracle.seq(rp, ci, n, Y0, T, k, dict(eta0=1.0, total_epochs=T), seed=1)
+    u_full = oracle.objective(rp, ci, n, Y, k)["total"]
+    u_seq = oracle.objective(rp, ci, n, S, k)["total"]
+    u_start = oracle.objective(rp, ci, n, Y0, k)["total"]
+    assert u_full < 0.5 * u_start
+    assert abs(u_seq / u_full - 1) < 0.02
+    np_full = oracle.neighborhood_preservation(rp, ci, n, Y)
+    np_seq = oracle.neighborhood_preservation(rp, ci, n, S)
+    assert abs(np_seq - np_full) < 0.02
