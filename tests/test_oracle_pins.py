@@ -447,3 +447,33 @@ def test_algorithm1_reaches_the_objective_of_full_gradient_descent():
     np_full = oracle.neighborhood_preservation(rp, ci, n, Y)
     np_seq = oracle.neighborhood_preservation(rp, ci, n, S)
     assert abs(np_seq - np_full) < 0.02
+
+
+# --------------------------------------------------------------------------
+# Section 3.2: with the linear degree weight, inter-community connectivity
+# maps to spatial proximity (the paper's light-blue class sits nearer the
+# class it shares more edges with).  Four planted blocks of 150; pairs (A, B)
+# and (C, D) share three times the edge density of the other pairs.
+# --------------------------------------------------------------------------
+def _four_blocks(seed):
+    rng = np.random.default_rng(seed)
+    n, lab = 600, np.repeat(np.arange(4), 150)
+    iu, ju = np.triu_indices(n, 1)
+    a, b = lab[iu], lab[ju]
+    strong = ((a == 0) & (b == 1)) | ((a == 2) & (b == 3))
+    p = np.where(a == b, 0.08, np.where(strong, 0.006, 0.002))
+    hit = rng.random(iu.size) < p
+    rp, ci = edges_to_csr(n, iu[hit], ju[hit])
+    return n, rp, ci, lab
+
+
+def test_connectivity_maps_to_proximity():
+    strong, weak = [], []
+    for seed in range(1, 6):
+        n, rp, ci, lab = _four_blocks(seed)
+        Y = oracle.seq(rp, ci, n, initial_positions(n, seed), 30, 3, dict(eta0=1.0, total_epochs=30), seed=seed)
+        c = np.array([Y[lab == q].mean(0) for q in range(4)])
+        for x in range(4):
+            for y in range(x + 1, 4):
+                (strong if (x, y) in ((0, 1), (2, 3)) else weak).append(np.linalg.norm(c[x] - c[y]))
+    assert np.mean(strong) < 0.85 * np.mean(weak)
