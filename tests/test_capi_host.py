@@ -162,3 +162,21 @@ def test_reorder_rejects_bad_input(lib):
     rp = np.array([0, 1, 2], np.int64)
     assert _status(snap.snap_graph_reorder, rp, np.array([1, 5], np.int32))[0] == 1
     assert _status(snap.snap_graph_reorder, rp, np.array([1, 1], np.int32))[0] == 1
+
+
+def test_batch_union_is_a_disjoint_union():
+    from synth import tiny_graph
+    graphs = [tiny_graph(n, m, seed=s) for s, (n, m) in enumerate([(30, 60), (1, 0), (50, 120), (7, 9)])]
+    rp, ci, offs = snap.batch_union([(g.row_ptr, g.col_idx) for g in graphs])
+    assert rp.dtype == np.int64 and ci.dtype == np.int32 and offs.dtype == np.int32
+    assert offs.tolist() == [0, 30, 31, 81, 88] and rp.size == 89
+    assert rp[-1] == sum(int(g.row_ptr[-1]) for g in graphs) == ci.size
+    for q, g in enumerate(graphs):
+        a, b = int(offs[q]), int(offs[q + 1])
+        sub_rp = rp[a:b + 1] - rp[a]
+        sub_ci = ci[rp[a]:rp[b]] - a
+        assert np.array_equal(sub_rp, g.row_ptr) and np.array_equal(sub_ci, g.col_idx)
+    # no edge leaves its graph
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    graph_of = np.searchsorted(offs, np.arange(rp.size - 1), side="right") - 1
+    assert np.array_equal(graph_of[rows], graph_of[ci])
