@@ -185,6 +185,22 @@ def oracle_sampler(name, row_ptr):
     return oracle.Sampler.degree(row_ptr) if name == "degree" else None
 
 
+def host_info():
+    """Logical cores and CPU model of the host the oracle runs on."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part"):
+                    model = f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
 def cpu_baseline(n, row_ptr, col_idx, Y0, k, sample_edges, seed, sampler="uniform"):
     """The FP64 oracle (Algorithm 1, one host core) on a bounded sample: one
     epoch limited to the first `sample_edges` directed edges of its shuffled
@@ -201,7 +217,7 @@ def cpu_baseline(n, row_ptr, col_idx, Y0, k, sample_edges, seed, sampler="unifor
     work = max(t_run - t_shuffle, 1e-9)
     done = min(int(sample_edges), int(row_ptr[-1]))   # directed edges the sampled epoch visits
     upd = done * (1 + k)
-    return {"value": upd / work, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": upd / work, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"1 epoch of the same graph limited to {done} of {int(row_ptr[-1])} directed edges "
                       f"({upd} pair updates, FP64, 1 thread); edge-list shuffle {t_shuffle:.2f} s excluded",
             "seconds": work}
@@ -252,7 +268,7 @@ def run_reference(args, rank, world):
             "data": "synthetic", "s_per_layout_extrapolated": per_layout,
             "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{args.k}-{EPOCHS}ep-bfs", "n": n,
                        "undirected_edges": args.edges, "k": args.k, "epochs": EPOCHS, "sampler": args.sampler},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"each step: 1 epoch limited to {done} of {int(row_ptr[-1])} directed "
                                        f"edges, FP64 Algorithm 1, "
                                        f"1 thread; shuffle ({t_shuffle:.2f} s, once per layout) excluded"},

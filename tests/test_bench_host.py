@@ -30,6 +30,7 @@ def test_reference_line_counts_the_edges_it_visits():
     assert d["config"]["workload"].startswith("rmat12-30000e-k3")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["cpu"]
     assert "60000 of 60000 directed edges" in cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     # one step is one sampled epoch: every directed edge of this small graph, (1 + k) pair updates each
