@@ -41,6 +41,26 @@ def test_every_declared_symbol_is_exported(lib):
         assert re.search(rf"\bT {nm}\b", out), nm
 
 
+def _declared_parameter_counts():
+    """Parameter count of every function declared in the header (comments removed)."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(snap_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_header(lib):
+    counts = _declared_parameter_counts()
+    assert counts["snap_layout_autotune"] == 12 and counts["snap_layout_epochs"] == 8
+    for name, k in counts.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None, f"{name} has no argtypes in the binding"
+        assert len(argtypes) == k, f"{name}: header {k} parameters, binding {len(argtypes)}"
+
+
 def test_struct_layouts_match_header(lib):
     src = r'''
 #include <stdio.h>
