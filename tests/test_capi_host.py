@@ -41,24 +41,36 @@ def test_every_declared_symbol_is_exported(lib):
         assert re.search(rf"\bT {nm}\b", out), nm
 
 
-def _declared_parameter_counts():
-    """Parameter count of every function declared in the header (comments removed)."""
+def _declared_parameters():
+    """Parameter declarations of every function in the header (comments removed)."""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     out = {}
     for m in re.finditer(r"\b(snap_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
         params = m.group(2).strip()
-        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+        out[m.group(1)] = [] if params in ("", "void") else [re.sub(r"\s+", " ", p.strip())
+                                                               for p in params.split(",")]
     return out
 
 
-def test_binding_argument_counts_match_header(lib):
-    counts = _declared_parameter_counts()
-    assert counts["snap_layout_autotune"] == 12 and counts["snap_layout_epochs"] == 8
-    for name, k in counts.items():
+def _ctypes_of(decl):
+    """The ctypes type a C parameter declaration is passed as."""
+    if "*" in decl or decl.startswith(("snap_layout_t ", "snap_multi_t ")):
+        return ctypes.c_void_p
+    base = decl.rsplit(" ", 1)[0].replace("const ", "")
+    return {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+            "double": ctypes.c_double, "float": ctypes.c_float}[base]
+
+
+def test_binding_arguments_match_header(lib):
+    decls = _declared_parameters()
+    assert len(decls["snap_layout_autotune"]) == 12 and len(decls["snap_layout_epochs"]) == 8
+    for name, params in decls.items():
         argtypes = getattr(lib, name).argtypes
         assert argtypes is not None, f"{name} has no argtypes in the binding"
-        assert len(argtypes) == k, f"{name}: header {k} parameters, binding {len(argtypes)}"
+        assert len(argtypes) == len(params), f"{name}: header {len(params)} parameters, binding {len(argtypes)}"
+        for decl, t in zip(params, argtypes):
+            assert t == _ctypes_of(decl), f"{name}: '{decl}' passed as {t.__name__}"
 
 
 def test_struct_layouts_match_header(lib):
