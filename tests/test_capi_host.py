@@ -71,6 +71,15 @@ def test_binding_arguments_match_header(lib):
         assert len(argtypes) == len(params), f"{name}: header {len(params)} parameters, binding {len(argtypes)}"
         for decl, t in zip(params, argtypes):
             assert t == _ctypes_of(decl), f"{name}: '{decl}' passed as {t.__name__}"
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    returns = {"void": None, "snap_status": ctypes.c_int, "int64_t": ctypes.c_int64, "const char *": ctypes.c_char_p}
+    decl_re = r"(?:^|\n)\s*((?:const\s+)?[a-z_0-9]+\s*\**)\s*(snap_[a-z_]+)\s*\([^;{]*?\)\s*;"
+    seen = 0
+    for m in re.finditer(decl_re, text, flags=re.S):
+        ret = re.sub(r"\s+", " ", m.group(1).strip()).replace(" *", " *")
+        assert getattr(lib, m.group(2)).restype == returns[ret], m.group(2)
+        seen += 1
+    assert seen == len(decls)
 
 
 def test_struct_layouts_match_header(lib):
