@@ -16,7 +16,13 @@ Parity status per function:
   epoch_displacement          pinned (Monte-Carlo mean -> -2 grad U, Section 3.3)
   seq (Algorithm 1)           pinned (two-node closed form, n = 2 forced draw,
                               centroid invariance, rotation equivariance,
-                              actual-vs-effective energy of Fig. 3)
+                              actual-vs-effective energy of Fig. 3a, the
+                              objective and NP of full-gradient descent on
+                              Eq. 4 (Fig. 3b), connectivity mapped to
+                              proximity (Section 3.2))
+  edge_negatives (uniform)    pinned (one epoch's updates obey Section 3.4's
+                              sparsity: Delta ~ d_max/|E| + k/(|V|-1),
+                              conflict probability <= (k+2) Delta)
   sync                        pinned (S = 1 equals Y + eta * displacement;
                               chunk bounds by hand; cap by closed form)
   neighborhood_preservation   pinned (hand-computed 6-node case, lattice case)
