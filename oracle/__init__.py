@@ -25,6 +25,11 @@ Parity status per function:
                               conflict probability <= (k+2) Delta)
   sync                        pinned (S = 1 equals Y + eta * displacement;
                               chunk bounds by hand; cap by closed form)
+  sync_chunks                 pinned (one chunk of one equals Y + eta *
+                              displacement at any Y and epoch; the chunks'
+                              moves from one Y add up to it; a chunk moves
+                              only the vertices its rows touch; chunks in
+                              order equal sync's epoch)
   neighborhood_preservation   pinned (hand-computed 6-node case, lattice case)
   alias_build                 pinned (hand-worked two-node table; the table's
                               exact distribution equals q/Q within 2^-32 per
@@ -96,6 +101,8 @@ def _load():
     lib.oracle_epoch_displacement.restype = ctypes.c_int
     lib.oracle_sync.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, f64, P, P]
     lib.oracle_sync.restype = ctypes.c_int
+    lib.oracle_sync_chunks.argtypes = [P, P, i32, P, i32, i32, i32, i32, i32, i32, f64, f64, i32, u64, f64, P, P]
+    lib.oracle_sync_chunks.restype = ctypes.c_int
     lib.oracle_objective.argtypes = [P, P, i32, P, i32, P, P]
     lib.oracle_objective.restype = ctypes.c_int
     lib.oracle_objective_sampled.argtypes = [P, P, i32, P, i32, i64, u64, P, P]
@@ -279,6 +286,23 @@ def sync(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, substeps=1, 
     if rc != 0:
         raise MemoryError("oracle_sync failed to allocate")
     return Y
+
+
+def sync_chunks(row_ptr, col_idx, n, Y, t, c_begin, c_end, substeps, k, schedule=None, seed=1, cap=0.0,
+                sampler=None):
+    """Chunks [c_begin, c_end) of `substeps` of epoch t of the synchronous
+    mode, started from Y (any positions, e.g. another implementation's at a
+    chunk boundary).  Returns the (n,2) float64 result."""
+    rp, ci = _csr(row_ptr, col_idx)
+    Yd = _positions(Y).copy()
+    kind, eta0, eta_min, total = _sched(schedule)
+    rc = _load().oracle_sync_chunks(_p(rp), _p(ci), n, _p(Yd), t, c_begin, c_end, substeps, k, kind, eta0,
+                                    eta_min, total, seed, cap, *_tables(sampler))
+    if rc == -2:
+        raise ValueError("chunk range outside [0, substeps]")
+    if rc != 0:
+        raise MemoryError("oracle_sync_chunks failed to allocate")
+    return Yd
 
 
 def objective(row_ptr, col_idx, n, Y, k, sampler=None) -> dict:

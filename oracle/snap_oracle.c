@@ -115,7 +115,8 @@ uint32_t oracle_edge_word(uint64_t e, uint32_t t, uint32_t w, uint64_t seed)
     return out[w % 4u];
 }
 
-/* Uniform draw from V \ {i} (Algorithm 1, "Sample y_s ~ Uniform(Y \ {y_i})"). */
+/* Uniform draw over every vertex except the source i (the negative sample of
+ * Algorithm 1). */
 int32_t oracle_uniform_negative(uint32_t word, int32_t i, int32_t n)
 {
     uint32_t u = (uint32_t)(((uint64_t)word * (uint64_t)(uint32_t)(n - 1)) >> 32);
@@ -508,6 +509,30 @@ int oracle_epoch_displacement(const int64_t *row_ptr, const int32_t *col_idx, in
     return 0;
 }
 
+/* One chunk step of the synchronous mode: the forces of the edges of rows
+ * [r0, r1) and of their negatives, summed from Y frozen at the chunk's start
+ * (D is n x 2 scratch), then Y += eta * D, each vertex's step clipped to
+ * length `limit` when limit > 0. */
+static void sync_chunk_step(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double *Y,
+                            int32_t r0, int32_t r1, int32_t k, uint32_t t, uint64_t seed, double eta,
+                            double limit, const uint32_t *prob, const int32_t *alias, double *D)
+{
+    memset(D, 0, sizeof(double) * 2 * (size_t)n);
+    chunk_displacement(row_ptr, col_idx, n, Y, r0, r1, k, t, seed, prob, alias, D);
+    for (int32_t i = 0; i < n; ++i) {
+        double sx = eta * D[2 * (int64_t)i], sy = eta * D[2 * (int64_t)i + 1];
+        if (limit > 0.0) {
+            double len = sqrt(sx * sx + sy * sy);
+            if (len > limit) {
+                sx *= limit / len;
+                sy *= limit / len;
+            }
+        }
+        Y[2 * (int64_t)i] += sx;
+        Y[2 * (int64_t)i + 1] += sy;
+    }
+}
+
 /* Synchronous mode: per epoch, S chunks of rows; for each chunk the forces of
  * its edges and negatives are summed from positions frozen at the chunk's
  * start, then Y += eta_t * D.  With cap > 0 each node's step is clipped to
@@ -530,25 +555,41 @@ int oracle_sync(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, doubl
     for (int32_t ep = 0; ep < epochs; ++ep) {
         int32_t t = epoch_begin + ep;
         double eta = oracle_step_size(sched_kind, eta0, eta_min, total_epochs, t);
-        for (int32_t c = 0; c < S; ++c) {
-            memset(D, 0, sizeof(double) * 2 * (size_t)n);
-            chunk_displacement(row_ptr, col_idx, n, Y, bound[c], bound[c + 1], k, (uint32_t)t, seed, prob, alias,
-                               D);
-            double limit = cap * eta / eta0;
-            for (int32_t i = 0; i < n; ++i) {
-                double sx = eta * D[2 * (int64_t)i], sy = eta * D[2 * (int64_t)i + 1];
-                if (cap > 0.0) {
-                    double len = sqrt(sx * sx + sy * sy);
-                    if (len > limit) {
-                        sx *= limit / len;
-                        sy *= limit / len;
-                    }
-                }
-                Y[2 * (int64_t)i] += sx;
-                Y[2 * (int64_t)i + 1] += sy;
-            }
-        }
+        double limit = cap > 0.0 ? cap * eta / eta0 : 0.0;
+        for (int32_t c = 0; c < S; ++c)
+            sync_chunk_step(row_ptr, col_idx, n, Y, bound[c], bound[c + 1], k, (uint32_t)t, seed, eta, limit,
+                            prob, alias, D);
     }
+    free(D);
+    free(bound);
+    return 0;
+}
+
+/* Chunks [c_begin, c_end) of S of epoch t of the synchronous mode, applied to
+ * Y in order: the same steps oracle_sync takes for those chunks, started
+ * from whatever Y the caller passes (e.g. another implementation's positions
+ * at a chunk boundary).  Returns 0, -1 on allocation failure, -2 on a bad
+ * chunk range. */
+int oracle_sync_chunks(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double *Y, int32_t t,
+                       int32_t c_begin, int32_t c_end, int32_t S, int32_t k, int32_t sched_kind, double eta0,
+                       double eta_min, int32_t total_epochs, uint64_t seed, double cap, const uint32_t *prob,
+                       const int32_t *alias)
+{
+    if (S < 1 || c_begin < 0 || c_end > S || c_begin > c_end)
+        return -2;
+    double *D = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    int32_t *bound = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S + 1));
+    if (!D || !bound) {
+        free(D);
+        free(bound);
+        return -1;
+    }
+    oracle_sync_chunk_bounds(row_ptr, n, S, bound);
+    double eta = oracle_step_size(sched_kind, eta0, eta_min, total_epochs, t);
+    double limit = cap > 0.0 ? cap * eta / eta0 : 0.0;
+    for (int32_t c = c_begin; c < c_end; ++c)
+        sync_chunk_step(row_ptr, col_idx, n, Y, bound[c], bound[c + 1], k, (uint32_t)t, seed, eta, limit, prob,
+                        alias, D);
     free(D);
     free(bound);
     return 0;

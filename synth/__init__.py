@@ -17,4 +17,6 @@ from .graphs import (  # noqa: F401
     serving_graph_pool,
     initial_positions,
     tiny_graph,
+    bfs_relabel,
+    source_digest,
 )

@@ -269,6 +269,7 @@ def rmat_graph(scale: int = 22, num_edges: int = 34_000_000, a: float = 0.57, b:
 
 
 _NATIVE = None
+_NATIVE_SOURCES = ("rmat_native.c", "relabel.c")
 
 
 def _native_lib():
@@ -279,17 +280,20 @@ def _native_lib():
     import ctypes
     import subprocess
     here = os.path.dirname(os.path.abspath(__file__))
-    src = os.path.join(here, "rmat_native.c")
+    srcs = [os.path.join(here, f) for f in _NATIVE_SOURCES]
     lib = os.path.join(here, "librmat_native.so")
-    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(s) for s in srcs):
         tmp = lib + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src])
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, *srcs])
         os.replace(tmp, lib)
     L = ctypes.CDLL(lib)
     L.rmat_native_generate.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p]
     L.rmat_native_generate.restype = ctypes.c_int
+    L.synth_bfs_relabel.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]
+    L.synth_bfs_relabel.restype = ctypes.c_int
     _NATIVE = L
     return L
 
@@ -310,6 +314,46 @@ def rmat_graph_native(scale: int, num_edges: int, a: float = 0.57, b: float = 0.
         raise MemoryError(f"rmat_native_generate failed ({rc})")
     return Graph(n, row_ptr, col_idx, name=f"rmat-native-s{scale}-e{num_edges}-s{seed}",
                  meta=dict(a=a, b=b, c=c, d=1 - a - b - c, seed=seed))
+
+
+def bfs_relabel(g: Graph) -> Graph:
+    """Breadth-first locality relabelling (synth/relabel.c): searches start at
+    the highest-degree vertex not reached yet (ties: smaller id), a vertex
+    appends its unreached neighbours in ascending id order, isolated vertices
+    come last; rows of the result are sorted ascending.  The relabelled graph
+    keeps ``meta["perm"]`` (new label of each old vertex)."""
+    n = g.n
+    perm = np.empty(n, dtype=np.int32)
+    rp = np.empty(n + 1, dtype=np.int64)
+    ci = np.empty(g.nnz, dtype=np.int32)
+    src_rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+    src_ci = np.ascontiguousarray(g.col_idx, dtype=np.int32)
+    rc = _native_lib().synth_bfs_relabel(src_rp.ctypes.data, src_ci.ctypes.data, n, perm.ctypes.data,
+                                         rp.ctypes.data, ci.ctypes.data)
+    if rc == -1:
+        raise MemoryError("synth_bfs_relabel: allocation failed")
+    if rc != 0:
+        raise ValueError("synth_bfs_relabel: malformed CSR")
+    labels = None
+    if g.labels is not None:
+        labels = np.empty_like(g.labels)
+        labels[perm] = g.labels
+    meta = dict(g.meta)
+    meta["perm"] = perm
+    return Graph(n, rp, ci, labels=labels, name=g.name + "-bfs", meta=meta)
+
+
+def source_digest() -> str:
+    """Hash of the generator sources (this module and the C files): the key
+    under which a generated input may be cached on disk, so that a change to
+    a generator never reuses a stale graph."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    h = hashlib.sha256()
+    for f in ("graphs.py",) + _NATIVE_SOURCES:
+        with open(os.path.join(here, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def planted_partition_graph(n: int, communities: int, avg_degree: float, mu: float, rng: np.random.Generator,

@@ -221,3 +221,19 @@ def test_batch_union_is_a_disjoint_union():
     rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
     graph_of = np.searchsorted(offs, np.arange(rp.size - 1), side="right") - 1
     assert np.array_equal(graph_of[rows], graph_of[ci])
+
+
+@pytest.mark.parametrize("gen", ["tiny", "sbm", "rmat"])
+def test_synth_relabel_gives_the_library_relabelling(lib, gen):
+    """The input generators relabel graphs with their own code (so the
+    oracle's inputs never pass through the library); both must give the same
+    labels and the same CSR, so that both arms of the bench and the stored
+    oracle values see the graph the library lays out."""
+    from synth import bfs_relabel
+    g = {"tiny": lambda: tiny_graph(300, 700, seed=2),
+         "sbm": lambda: sbm_graph(n=500, blocks=5, p_in=0.05, p_out=0.002, seed=3),
+         "rmat": lambda: rmat_graph(scale=14, num_edges=60000, seed=4)}[gen]()
+    perm, rp, ci = snap.snap_graph_reorder(g.row_ptr, g.col_idx)
+    r = bfs_relabel(g)
+    assert np.array_equal(r.meta["perm"], perm)
+    assert np.array_equal(r.row_ptr, rp) and np.array_equal(r.col_idx, ci)

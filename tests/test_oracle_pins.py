@@ -333,6 +333,50 @@ def test_sync_chunk_bounds_by_hand():
     assert list(oracle.sync_chunk_bounds(rp, 6, 24)) == [0] + [1] * 5 + [2, 3] + [4] * 13 + [6] * 3 + [6]
 
 
+def test_sync_chunks_partition_the_frozen_displacement():
+    # chunk c of S from Y moves Y by eta * (the forces of the edges of its rows
+    # and their negatives); the chunks partition the rows, so the moves of all
+    # chunks, each taken from the same Y, add up to the one-chunk step, which
+    # is Y + eta * (the frozen displacement of Section 3.3's estimate)
+    g = tiny_graph(60, 150, seed=12)
+    Y = initial_positions(g.n, 3).astype(np.float64) * 1.7
+    sched = dict(kind=0, eta0=0.8, eta_min=1e-3, total_epochs=10)
+    t, S = 4, 5
+    eta = oracle.step_size(sched, t)
+    D = oracle.epoch_displacement(g.row_ptr, g.col_idx, g.n, Y, t, 3, 21)
+    one = oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y, t, 0, 1, 1, 3, sched, seed=21)
+    assert np.allclose(one, Y + eta * D, rtol=0, atol=1e-14)
+    moves = sum(oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y, t, c, c + 1, S, 3, sched, seed=21) - Y
+                for c in range(S))
+    assert np.allclose(moves, eta * D, rtol=0, atol=1e-13)
+    # each chunk moves only the sources of its rows, their partners and drawn negatives
+    b = oracle.sync_chunk_bounds(g.row_ptr, g.n, S)
+    for c in range(S):
+        step = oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y, t, c, c + 1, S, 3, sched, seed=21) - Y
+        touched = set()
+        for i in range(b[c], b[c + 1]):
+            for e in range(g.row_ptr[i], g.row_ptr[i + 1]):
+                touched |= {i, int(g.col_idx[e])}
+                touched |= {oracle.uniform_negative(oracle.edge_word(e, t, m, 21), i, g.n) for m in range(3)}
+        moved = set(np.flatnonzero(np.abs(step).sum(axis=1) > 0).tolist())
+        assert moved <= touched
+
+
+def test_sync_chunks_in_order_are_one_synchronous_epoch():
+    g = tiny_graph(80, 200, seed=13)
+    Y0 = initial_positions(g.n, 4).astype(np.float64)
+    sched = dict(kind=0, eta0=1.0, eta_min=1e-3, total_epochs=30)
+    S, cap, t = 6, 0.05, 2
+    want = oracle.sync(g.row_ptr, g.col_idx, g.n, Y0, 1, 3, sched, seed=5, substeps=S, cap=cap, epoch_begin=t)
+    Y = Y0
+    for c in range(S):
+        Y = oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y, t, c, c + 1, S, 3, sched, seed=5, cap=cap)
+    assert np.array_equal(Y, want)
+    assert np.array_equal(oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y0, t, 2, 2, S, 3, sched, seed=5), Y0)
+    with pytest.raises(ValueError):
+        oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y0, t, 3, 7, S, 3, sched, seed=5)
+
+
 def test_sync_cap_clips_step_length():
     rp, ci = _two_node()
     Y0 = np.array([[0.0, 0.0], [3.0, 4.0]])
