@@ -212,6 +212,33 @@ snap_status snap_layout_epochs(snap_layout_t h, float *positions, int32_t epoch_
                                void *cuda_stream);
 
 /*
+ * snap_layout_sync_chunks -- run chunks [chunk_begin, chunk_end) of epoch
+ * `epoch` of the synchronous mode (SNAP_MODE_SYNC handles only).
+ *
+ * Paper: none directly.  The synchronous mode is this library's
+ * deterministic variant of Algorithm 1 (Section 3.3's update with positions
+ * frozen within a chunk of rows); an epoch is sync_substeps chunk steps, each
+ * summing the forces of its rows' edges and negatives from the positions at
+ * the chunk's start and then applying eta_epoch times that sum (clipped to
+ * sync_cap * eta_epoch / eta0 per vertex when sync_cap > 0).
+ *
+ *   positions    device, n x 2 float32, updated in place.
+ *   epoch        the epoch index t (selects the step size and the random words).
+ *   chunk_begin, chunk_end   0 <= chunk_begin <= chunk_end <= sync_substeps.
+ *   neg_samples, schedule, seed   as for snap_layout_epochs.
+ *
+ * Calling it for chunks [0, c) and then [c, sync_substeps) gives bit for bit
+ * the positions of one snap_layout_epochs call for that epoch, so an epoch
+ * can be split at any chunk boundary (to interleave other work, or to look at
+ * the positions between chunks).  Asynchronous, like snap_layout_epochs.
+ * Errors: INVALID_ARG (not a SYNC handle, range outside [0, sync_substeps],
+ * bad schedule or k), CUDA, NUMERIC (from an earlier call).
+ */
+snap_status snap_layout_sync_chunks(snap_layout_t h, float *positions, int32_t epoch,
+                                    int32_t chunk_begin, int32_t chunk_end, int32_t neg_samples,
+                                    const snap_schedule *schedule, uint64_t seed, void *cuda_stream);
+
+/*
  * snap_layout_epochs_energy -- snap_layout_epochs that also reports the
  * "actual energy" of every epoch (Section 3.3, compared there with the
  * effective energy of Eq. 4 evaluated after each epoch): half the sum, over
@@ -367,26 +394,34 @@ snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int3
  * inside the library, sized for at most 262,144 vertices (4 MiB, present on
  * every GPU that loads the library until the process exits).
  *
- *   row_ptr, col_idx  DEVICE, caller-owned, the symmetric CSR contract of
- *                     snap_layout_create (not re-validated; a column outside
- *                     [0, n) is skipped and reported as INVALID_ARG).
+ *   row_ptr, col_idx  DEVICE, caller-owned, on the current device: the
+ *                     symmetric CSR of snap_layout_create (n + 1 int64 and
+ *                     nnz int32 entries).
+ *   nnz               number of entries of col_idx, 0 <= nnz < 2^32.
  *   n                 1 <= n <= 262,144, else INVALID_ARG.
- *   positions         device, n x 2 float32, updated in place.
+ *   positions         device, n x 2 float32, on the current device, updated
+ *                     in place.
  *   epoch_begin, epochs, neg_samples, schedule, seed
  *                     as snap_layout_epochs.
  *   substeps, cap     as snap_options.sync_substeps / sync_cap.
  *
- * The result equals snap_layout_epochs on a SNAP_MODE_SYNC handle with the
- * same substeps and cap (default 32-edge segments).  The first call on a
- * device looks up the scratch's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls in the process share
- * the scratch, which keeps the last call's contents (each call clears it
- * first): calls that overlap on the GPU -- other streams, other host
- * threads -- race and must be serialised by the caller.  Waits for the
- * stream before returning.  Errors: INVALID_ARG, CUDA, NUMERIC.
+ * Before any epoch runs, the CSR is checked on the device with the rules of
+ * snap_layout_create (row_ptr[0] = 0, row_ptr[n] = nnz, non-decreasing;
+ * columns in [0, n), no self-loop, rows strictly ascending, every edge's
+ * reverse present); a violation returns INVALID_ARG with the positions
+ * untouched.  A buffer that is not device memory of the current device is
+ * INVALID_ARG too.  The result equals snap_layout_epochs on a
+ * SNAP_MODE_SYNC handle with the same substeps and cap (default 32-edge
+ * segments).  The first call on a device looks up the scratch's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls in the process share the scratch, which keeps the last
+ * call's contents (each call clears it first): calls that overlap on the GPU
+ * -- other streams, other host threads -- race and must be serialised by the
+ * caller.  Waits for the stream (after the check and at the end) before
+ * returning.  Errors: INVALID_ARG, CUDA, NUMERIC.
  */
-snap_status snap_sync_epochs_noalloc(const int64_t *row_ptr, const int32_t *col_idx, int32_t n,
-                                     float *positions, int32_t epoch_begin, int32_t epochs,
+snap_status snap_sync_epochs_noalloc(const int64_t *row_ptr, const int32_t *col_idx, int64_t nnz,
+                                     int32_t n, float *positions, int32_t epoch_begin, int32_t epochs,
                                      int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
                                      int32_t substeps, float cap, void *cuda_stream);
 

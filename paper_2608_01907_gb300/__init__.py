@@ -23,7 +23,7 @@ __all__ = [
     "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
     "snap_layout_run", "snap_last_error", "Layout", "linear_schedule", "snap_sync_epochs_noalloc",
     "snap_layout_create_batch", "batch_union", "snap_layout_autotune", "MultiEpoch", "snap_sampler_table",
-    "snap_layout_epochs_energy",
+    "snap_layout_epochs_energy", "snap_layout_sync_chunks",
 ]
 
 MODE_HOGWILD, MODE_HOGWILD_RED, MODE_SYNC = 0, 1, 2
@@ -91,6 +91,8 @@ def load_library():
     lib.snap_layout_epochs.restype = st
     lib.snap_layout_epochs_energy.argtypes = [P, P, i32, i32, i32, P, u64, P, P]
     lib.snap_layout_epochs_energy.restype = st
+    lib.snap_layout_sync_chunks.argtypes = [P, P, i32, i32, i32, i32, P, u64, P]
+    lib.snap_layout_sync_chunks.restype = st
     lib.snap_layout_objective.argtypes = [P, P, i32, i32, i64, u64, P, P, P, P]
     lib.snap_layout_objective.restype = st
     lib.snap_layout_check.argtypes = [P, P]
@@ -107,7 +109,7 @@ def load_library():
     lib.snap_graph_reorder.restype = st
     lib.snap_layout_run.argtypes = [P, P, i32, P, P, i32, i32, P, u64, P]
     lib.snap_layout_run.restype = st
-    lib.snap_sync_epochs_noalloc.argtypes = [P, P, i32, P, i32, i32, i32, P, u64, i32, ctypes.c_float, P]
+    lib.snap_sync_epochs_noalloc.argtypes = [P, P, i64, i32, P, i32, i32, i32, P, u64, i32, ctypes.c_float, P]
     lib.snap_sync_epochs_noalloc.restype = st
     lib.snap_multi_create.argtypes = [i32, P]
     lib.snap_multi_create.restype = st
@@ -229,6 +231,13 @@ def snap_layout_epochs_energy(h, positions, epoch_begin: int, epochs: int, neg_s
                                                     ctypes.c_void_p(energy.data_ptr()), _stream(stream)))
 
 
+def snap_layout_sync_chunks(h, positions, epoch: int, chunk_begin: int, chunk_end: int, neg_samples: int,
+                            schedule: SnapSchedule, seed: int, stream=None) -> None:
+    """Chunks [chunk_begin, chunk_end) of epoch `epoch` of a SYNC handle."""
+    _check(load_library().snap_layout_sync_chunks(h, _device_positions(positions), epoch, chunk_begin, chunk_end,
+                                                  neg_samples, ctypes.byref(schedule), seed, _stream(stream)))
+
+
 def snap_layout_objective(h, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0,
                           seed: int = 0, stream=None) -> tuple[float, float, float]:
     a, r, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
@@ -340,19 +349,24 @@ def snap_sync_epochs_noalloc(row_ptr, col_idx, positions, epoch_begin: int, epoc
     """Synchronous epochs without any device allocation (see the C header).
 
     row_ptr (int64), col_idx (int32) and positions ((n, 2) float32) are CUDA
-    tensors the caller owns; n is positions.shape[0] (at most 262,144)."""
+    tensors the caller owns, all on one device; n is positions.shape[0] (at
+    most 262,144) and nnz is col_idx.numel().  The call runs with that device
+    current."""
     import torch
     for t, dt in ((row_ptr, torch.int64), (col_idx, torch.int32)):
         if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dt or not t.is_contiguous():
             raise TypeError("row_ptr / col_idx must be contiguous CUDA tensors (int64 / int32)")
     p = _device_positions(positions)
+    if not (row_ptr.device == col_idx.device == positions.device):
+        raise ValueError("row_ptr, col_idx and positions must be on the same CUDA device")
     n = int(positions.shape[0])
     if row_ptr.numel() != n + 1:
         raise ValueError("row_ptr must have n + 1 entries")
-    _check(load_library().snap_sync_epochs_noalloc(ctypes.c_void_p(row_ptr.data_ptr()),
-                                                   ctypes.c_void_p(col_idx.data_ptr()), n, p, epoch_begin, epochs,
-                                                   neg_samples, ctypes.byref(schedule), seed, substeps, cap,
-                                                   _stream(stream)))
+    with torch.cuda.device(positions.device):
+        _check(load_library().snap_sync_epochs_noalloc(ctypes.c_void_p(row_ptr.data_ptr()),
+                                                       ctypes.c_void_p(col_idx.data_ptr()), col_idx.numel(), n, p,
+                                                       epoch_begin, epochs, neg_samples, ctypes.byref(schedule),
+                                                       seed, substeps, cap, _stream(stream)))
 
 
 class MultiEpoch:
@@ -421,6 +435,12 @@ class Layout:
         _device_positions(positions, self.n)
         snap_layout_epochs_energy(self.handle, positions, epoch_begin, epochs, neg_samples, schedule, seed, energy,
                                   self.stream)
+
+    def sync_chunks(self, positions, epoch: int, chunk_begin: int, chunk_end: int, neg_samples: int,
+                    schedule: SnapSchedule, seed: int) -> None:
+        _device_positions(positions, self.n)
+        snap_layout_sync_chunks(self.handle, positions, epoch, chunk_begin, chunk_end, neg_samples, schedule, seed,
+                                self.stream)
 
     def objective(self, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0, seed: int = 0):
         _device_positions(positions, self.n)

@@ -773,6 +773,49 @@ static int inflight_grid(const snap_layout *h, int gmax) {
     return grid > 0 ? (int)grid : 1;
 }
 
+// Enqueues chunks [c_begin, c_end) of epoch t of the synchronous mode: for
+// each chunk, the frozen-position force sum of its rows (sync_chunk_kernel)
+// and the apply step (sync_apply_kernel).
+static cudaError_t enqueue_sync_chunks(snap_layout *h, float2 *pos, int32_t t, int32_t c_begin, int32_t c_end,
+                                       int32_t neg_samples, const snap_schedule &sched, uint64_t seed,
+                                       cudaStream_t stream, double *energy) {
+    const double eta = step_size(sched, t);
+    const double limit = h->opts.sync_cap > 0.0f ? (double)h->opts.sync_cap * eta / sched.eta0 : 0.0;
+    cudaError_t err = cudaSuccess;
+    for (int32_t c = c_begin; c < c_end && err == cudaSuccess; ++c) {
+        const int64_t eb = h->chunk_edges[(size_t)c], ee = h->chunk_edges[(size_t)c + 1];
+        if (ee > eb) {
+            SyncArgs a;
+            a.row_ptr = h->d_row_ptr;
+            a.col_idx = h->d_col;
+            a.seg_row = h->d_seg_row;
+            a.pos = pos;
+            a.disp = h->d_disp;
+            a.e_begin = eb;
+            a.e_end = ee;
+            a.n = h->n;
+            a.k = neg_samples;
+            a.seg_len = h->seg_len;
+            a.epoch = (uint32_t)t;
+            a.seed = seed;
+            a.status = h->d_status;
+            a.node_graph = h->d_node_graph;
+            a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
+            a.alias = h->d_alias;
+            a.energy = energy;
+            const int64_t segs = (ee + h->seg_len - 1) / h->seg_len - eb / h->seg_len;
+            const int64_t want = (segs + h->block - 1) / h->block;
+            const int grid = (int)(want < h->grid_sync ? want : h->grid_sync);
+            err = launch_sync_chunk(a, grid > 0 ? grid : 1, h->block, stream);
+        }
+        if (err == cudaSuccess)
+            err = launch_sync_apply(pos, h->d_disp, h->n, (float)eta, (float)limit, h->d_status, h->grid_apply, 256,
+                                    stream, h->d_node_graph, h->num_graphs > 1 ? h->d_graphs : nullptr, t,
+                                    h->opts.sync_cap);
+    }
+    return err;
+}
+
 // Enqueues the launches of epochs [epoch_begin, epoch_begin + epochs) on `stream`.
 static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_begin, int32_t epochs,
                                   int32_t neg_samples, const snap_schedule &sched, uint64_t seed,
@@ -784,39 +827,8 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
         const int32_t t = epoch_begin + ep;
         const double eta = step_size(*schedule, t);
         if (h->opts.mode == SNAP_MODE_SYNC) {
-            const double limit = h->opts.sync_cap > 0.0f ? (double)h->opts.sync_cap * eta / schedule->eta0 : 0.0;
-            const int32_t S = h->opts.sync_substeps;
-            for (int32_t c = 0; c < S && err == cudaSuccess; ++c) {
-                const int64_t eb = h->chunk_edges[(size_t)c], ee = h->chunk_edges[(size_t)c + 1];
-                if (ee > eb) {
-                    SyncArgs a;
-                    a.row_ptr = h->d_row_ptr;
-                    a.col_idx = h->d_col;
-                    a.seg_row = h->d_seg_row;
-                    a.pos = pos;
-                    a.disp = h->d_disp;
-                    a.e_begin = eb;
-                    a.e_end = ee;
-                    a.n = h->n;
-                    a.k = neg_samples;
-                    a.seg_len = h->seg_len;
-                    a.epoch = (uint32_t)t;
-                    a.seed = seed;
-                    a.status = h->d_status;
-                    a.node_graph = h->d_node_graph;
-                    a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
-                    a.alias = h->d_alias;
-                    a.energy = energy ? energy + ep : nullptr;
-                    const int64_t segs = (ee + h->seg_len - 1) / h->seg_len - eb / h->seg_len;
-                    const int64_t want = (segs + h->block - 1) / h->block;
-                    const int grid = (int)(want < h->grid_sync ? want : h->grid_sync);
-                    err = launch_sync_chunk(a, grid > 0 ? grid : 1, h->block, stream);
-                }
-                if (err == cudaSuccess)
-                    err = launch_sync_apply(pos, h->d_disp, h->n, (float)eta, (float)limit, h->d_status,
-                                            h->grid_apply, 256, stream, h->d_node_graph,
-                                            h->num_graphs > 1 ? h->d_graphs : nullptr, t, h->opts.sync_cap);
-            }
+            err = enqueue_sync_chunks(h, pos, t, 0, h->opts.sync_substeps, neg_samples, *schedule, seed, stream,
+                                      energy ? energy + ep : nullptr);
         } else {
             OrientedArgs a;
             a.row_ptr = h->d_act_row_ptr;
@@ -988,6 +1000,41 @@ snap_status snap_layout_epochs_energy(snap_layout_t h, float *positions, int32_t
         return fail(SNAP_ERR_INVALID_ARG, "actual_energy must be a non-NULL 8-byte aligned device buffer");
     if (h->num_graphs > 1) return fail(SNAP_ERR_NOT_SUPPORTED, "the actual energy is reported for single graphs");
     return epochs_impl(h, positions, epoch_begin, epochs, neg_samples, schedule, seed, actual_energy, cuda_stream);
+}
+
+snap_status snap_layout_sync_chunks(snap_layout_t h, float *positions, int32_t epoch, int32_t chunk_begin,
+                                    int32_t chunk_end, int32_t neg_samples, const snap_schedule *schedule,
+                                    uint64_t seed, void *cuda_stream) {
+    NvtxRange nvtx_range("snap_layout_sync_chunks");
+    if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
+    if (h->opts.mode != SNAP_MODE_SYNC) return fail(SNAP_ERR_INVALID_ARG, "the handle is not in SNAP_MODE_SYNC");
+    if (!positions) return fail(SNAP_ERR_INVALID_ARG, "positions is NULL");
+    if (((uintptr_t)positions & 7u) != 0) return fail(SNAP_ERR_INVALID_ARG, "positions must be 8-byte aligned");
+    if (epoch < 0) return fail(SNAP_ERR_INVALID_ARG, "epoch must be >= 0");
+    if (chunk_begin < 0 || chunk_end > h->opts.sync_substeps || chunk_begin > chunk_end)
+        return fail(SNAP_ERR_INVALID_ARG, "chunk range [%d, %d) outside [0, %d]", chunk_begin, chunk_end,
+                    h->opts.sync_substeps);
+    if (neg_samples < 0 || neg_samples > 64)
+        return fail(SNAP_ERR_INVALID_ARG, "neg_samples = %d out of [0, 64]", neg_samples);
+    snap_status st = check_schedule(schedule);
+    if (st != SNAP_OK) return st;
+    st = poll_status(h);
+    if (st != SNAP_OK) return st;
+    if (h->nnz == 0 || chunk_begin == chunk_end) return SNAP_OK;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    cudaError_t err = set_batch_schedule(h, *schedule, seed, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "copy graph table");
+    err = enqueue_sync_chunks(h, reinterpret_cast<float2 *>(positions), epoch, chunk_begin, chunk_end, neg_samples,
+                              *schedule, seed, stream, nullptr);
+    if (err != cudaSuccess) return cuda_fail(err, "sync chunk launch");
+    if (!h->status_pending) {
+        err = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess) err = cudaEventRecord(h->status_event, stream);
+        if (err != cudaSuccess) return cuda_fail(err, "status read-back");
+        h->status_pending = true;
+    }
+    h->mark_use(stream);
+    return SNAP_OK;
 }
 
 snap_status snap_layout_check(snap_layout_t h, void *cuda_stream) {

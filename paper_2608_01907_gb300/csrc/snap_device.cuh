@@ -146,4 +146,100 @@ __device__ __forceinline__ bool finite2(float2 v) {
     return isfinite(v.x) && isfinite(v.y);
 }
 
+
+// Energies of Table 1 / Eq. 2 for the actual energy of an epoch (Section
+// 3.3): U^a = alpha (r^2/2 + beta/2 ln(1 + r^2)), U^r = 1 / (2 (1 + r^2)).
+__device__ __forceinline__ float attraction_energy(float dx, float dy) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    return kAlpha * fmaf(0.5f, r2, 0.5f * kBeta * log1pf(r2));
+}
+
+__device__ __forceinline__ float repulsion_energy(float dx, float dy) {
+    return 0.5f * __frcp_rn(1.0f + fmaf(dx, dx, dy * dy));
+}
+
+// Per-lane view of the graph the current segment belongs to.
+struct GraphCtx {
+    int32_t base;        // first vertex of the graph
+    uint32_t nm1;        // n_g - 1
+    int64_t edge_base;   // first directed edge of the graph (random-word index origin)
+    uint32_t epoch;      // the graph's epoch
+    float eta;
+    uint2 key;           // Philox key (the graph's seed)
+    bool active;
+};
+
+__device__ __forceinline__ int32_t negative_in(const GraphCtx &c, uint32_t w, int32_t src) {
+    return c.base + negative_of(w, src - c.base, c.nm1);
+}
+
+__device__ __forceinline__ uint4 words_in(const GraphCtx &c, int64_t e, uint32_t g) {
+    return edge_words(e - c.edge_base, c.epoch, g, c.key);
+}
+
+__device__ __forceinline__ WordCursor cursor_in(const GraphCtx &c, int64_t e) { return word_cursor(e - c.edge_base); }
+
+// Next weighted negative of source src (global ids); table = the graph's alias table.
+__device__ __forceinline__ int32_t weighted_in(const GraphCtx &c, WordCursor &wc, const uint2 *alias, int32_t src) {
+    return c.base + weighted_negative(wc, c.epoch, c.key, alias + c.base, c.nm1 + 1u, src - c.base);
+}
+
+// All force terms of directed edge e = (i, j) in the synchronous mode, with
+// positions frozen (read-only during the launch): the attraction of Table 1
+// and the repulsion of each of its k negatives (Algorithm 1's draws, in the
+// order they consume the edge's random words), each force quantised to int64
+// fixed point (2^-32, to_fixed).  The partner's and the negatives' terms are
+// added to disp with integer atomics; the source's are summed into accx /
+// accy, which the caller flushes once per row run.  Integer addition makes
+// the totals independent of the order of the terms.  Returns the energy of
+// the step's pairs at the frozen positions (U^a of (i, j) and U^r of each
+// drawn pair) when `energy` is set, else 0.  Shared by the synchronous chunk
+// kernel of a handle and by the allocation-free entry point.
+__device__ __forceinline__ float sync_edge_terms(const float2 *pos, long long *disp, const GraphCtx &c,
+                                                 const uint2 *alias, int32_t i, float2 yi, int32_t j, int64_t e,
+                                                 int32_t k, bool energy, long long &accx, long long &accy,
+                                                 uint32_t &flags) {
+    const float2 yj = __ldg(pos + j);
+    float en = 0.0f;
+    if (energy) en += attraction_energy(yi.x - yj.x, yi.y - yj.y);
+    const float2 f = attraction_on_i(yi.x - yj.x, yi.y - yj.y);
+    const long long fx = to_fixed(f.x, flags), fy = to_fixed(f.y, flags);
+    accx += fx;
+    accy += fy;
+    add_fixed(disp + 2 * (int64_t)j, -fx);
+    add_fixed(disp + 2 * (int64_t)j + 1, -fy);
+    WordCursor wc = cursor_in(c, e);
+    for (int g = 0; g * 4 < k; ++g) {
+        const int nm = k - 4 * g < 4 ? k - 4 * g : 4;
+        int32_t s[4];
+        float2 ys[4];
+        if (alias) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s[m] = m < nm ? weighted_in(c, wc, alias, i) : i;
+        } else {
+            const uint4 w = words_in(c, e, (uint32_t)g);
+            s[0] = negative_in(c, w.x, i);
+            s[1] = negative_in(c, w.y, i);
+            s[2] = negative_in(c, w.z, i);
+            s[3] = negative_in(c, w.w, i);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (m < nm) ys[m] = __ldg(pos + s[m]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (m < nm) {
+                if (energy) en += repulsion_energy(yi.x - ys[m].x, yi.y - ys[m].y);
+                const float2 gr = repulsion_on_i(yi.x - ys[m].x, yi.y - ys[m].y);
+                const long long gx = to_fixed(gr.x, flags), gy = to_fixed(gr.y, flags);
+                accx += gx;
+                accy += gy;
+                add_fixed(disp + 2 * (int64_t)s[m], -gx);
+                add_fixed(disp + 2 * (int64_t)s[m] + 1, -gy);
+            }
+        }
+    }
+    return en;
+}
+
 }  // namespace snap

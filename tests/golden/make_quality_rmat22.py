@@ -1,0 +1,90 @@
+"""Writes tests/golden/quality_rmat22_k3.txt: the FP64 oracle's layouts of the
+bench's workload graph, scored -- the stored side of the full-size Hogwild
+quality gate (tests/test_gpu_quality_rmat22.py).
+
+Workload: R-MAT 2^22 nodes / 34,000,000 undirected edges (a, b, c = .57, .19,
+.19, seed 1), BFS locality relabelling, k = 3 negatives, 30 epochs, linear
+step decay from eta0 = 1 (floor 1e-3 eta0), seeds 1..5 (initial positions and
+random words).  Each layout is Algorithm 1 in the oracle (FP64, the directed
+edge list shuffled once), scored by the oracle: the objective of Eq. 4 (exact
+edge sum plus 20,000,000 sampled vertex pairs, sample seed 99) and the
+neighbourhood preservation of Section 4.1 (r = 2) on 1,024 vertices drawn
+without replacement from the non-isolated ones (numpy PCG64 seed 2024).
+
+Calls only oracle/ and synth/.  About 15 minutes of one core per seed; the
+seeds run in a spawned process pool:
+
+    python tests/golden/make_quality_rmat22.py [--processes 5]
+"""
+import argparse
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+OUT = os.path.join(HERE, "quality_rmat22_k3.txt")
+SEEDS = (1, 2, 3, 4, 5)
+K, EPOCHS = 3, 30
+SCHED = dict(kind=0, eta0=1.0, eta_min=1e-3, total_epochs=EPOCHS)
+PAIRS, PAIR_SEED = 20_000_000, 99
+NP_NODES, NP_SEED = 1024, 2024
+
+
+def graph():
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from gpu_helpers import rmat22_bfs
+    return rmat22_bfs()
+
+
+def np_sample(row_ptr):
+    deg = np.diff(row_ptr)
+    cand = np.nonzero(deg > 0)[0]
+    return np.sort(np.random.default_rng(NP_SEED).choice(cand, NP_NODES, replace=False)).astype(np.int32)
+
+
+def score(g, Y):
+    import oracle
+    ob = oracle.objective_sampled(g.row_ptr, g.col_idx, g.n, Y, K, PAIRS, PAIR_SEED)["total"]
+    return ob, oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, Y, np_sample(g.row_ptr))
+
+
+def job(seed):
+    import oracle
+    from synth import initial_positions
+    g = graph()
+    t = time.time()
+    Y = oracle.seq(g.row_ptr, g.col_idx, g.n, initial_positions(g.n, seed), EPOCHS, K, SCHED, seed=seed)
+    secs = time.time() - t
+    ob, npv = score(g, Y)
+    return seed, ob, npv, secs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--processes", type=int, default=len(SEEDS))
+    args = ap.parse_args()
+    import oracle
+    oracle.build()
+    graph()   # generate and cache once before the pool starts
+    with mp.get_context("spawn").Pool(args.processes) as pool:
+        rows = sorted(pool.map(job, SEEDS))
+    with open(OUT, "w") as f:
+        f.write("# FP64 oracle layouts (Algorithm 1) of R-MAT 2^22 / 34,000,000 edges, BFS relabelling,\n"
+                "# k = 3, 30 epochs, eta0 = 1 linear decay; scored by the oracle: objective of Eq. 4\n"
+                "# (exact edges + 20,000,000 sampled pairs, seed 99) and NP (Section 4.1, r = 2) on 1,024\n"
+                "# non-isolated vertices (PCG64 seed 2024).  Written by tests/golden/make_quality_rmat22.py.\n"
+                "# seed objective np oracle_seconds\n")
+        for seed, ob, npv, secs in rows:
+            f.write(f"{seed} {ob!r} {npv!r} {secs:.0f}\n")
+    print(open(OUT).read())
+
+
+if __name__ == "__main__":
+    main()

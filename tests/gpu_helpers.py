@@ -69,3 +69,46 @@ def gpu_layout(torch, g, Y0, epochs, k, sched, seed, opts=None, epoch_begin=0):
         L.check()
     torch.cuda.synchronize()
     return pos.cpu().numpy()
+
+
+def cached_graph(name: str, make):
+    """A generated input graph, cached on local disk under a key that includes
+    the hash of the generator sources (a changed generator never reuses a
+    stale graph).  `make()` returns a synth Graph."""
+    import os
+    import tempfile
+
+    from synth import Graph, source_digest
+    d = os.path.join(tempfile.gettempdir(), "snap_test_cache")
+    os.makedirs(d, exist_ok=True)
+    path = os.path.join(d, f"{name}_{source_digest()}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return Graph(int(z["n"]), z["row_ptr"], z["col_idx"], name=name)
+    g = make()
+    tmp = path + f".{os.getpid()}.npz"
+    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col_idx=g.col_idx)
+    os.replace(tmp, path)
+    return g
+
+
+def rmat22_bfs():
+    """The bench's workload graph: R-MAT 2^22 / 34,000,000 undirected edges,
+    BFS locality relabelling."""
+    from synth import bfs_relabel, rmat_graph
+    return cached_graph("rmat22_34m_bfs", lambda: bfs_relabel(rmat_graph(22, 34_000_000, seed=1)))
+
+
+def lfr260k():
+    """The LFR-style 260k-node / ~6.9M-edge community graph (seed 1)."""
+    from synth import lfr_graph
+    return cached_graph("lfr260k_s1", lambda: lfr_graph(seed=1))
+
+
+def coordinate_error(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Per-vertex parity error (max over the two coordinates), each relative
+    to max(|y|, rms(Y)) as in parity_error."""
+    ref = np.asarray(ref, dtype=np.float64)
+    gpu = np.asarray(gpu, dtype=np.float64)
+    scale = max(float(np.sqrt((ref ** 2).mean())), 1e-30)
+    return (np.abs(gpu - ref) / np.maximum(np.abs(ref), scale)).max(axis=1)

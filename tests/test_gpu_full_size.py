@@ -2,56 +2,37 @@
 (BFS relabelling), k = 3, in the launch configurations bench.py times.
 
 * SYNC (16 chunks, cap 1.0, the bench's synchronous configuration; and one
-  chunk without a cap): one epoch per coordinate against the oracle's
-  synchronous mode, every vertex, at eta0 = 0.01; at eta0 = 1 the chunked
-  Jacobi step amplifies FP32 rounding (see the test) and 99.9% of the
-  vertices meet the gate.
+  chunk without a cap): one whole epoch per coordinate against the oracle's
+  synchronous mode, every vertex, at eta0 = 0.01, where the chain of chunk
+  steps is well conditioned.  At eta0 = 1 every chunk step is checked on its
+  own in test_gpu_sync_chunks.py.
 * HOGWILD_RED (the bench's headline) and HOGWILD: one epoch from the same
   start against one epoch of Algorithm 1 (oracle, shuffled order): every
   position finite, and the decrease of the objective of Eq. 4 at least 3/4
-  of the oracle's (the first epoch, at eta0 = 1, depends strongly on the
-  visiting order; 30-epoch layouts are compared in quality_full_size.py).
+  of the oracle's.  The first epoch at eta0 = 1 moves vertices by up to 0.9
+  of their distance to a partner per step, so it depends strongly on the
+  visiting order; the 30-epoch layouts are gated at 2% of the oracle's in
+  test_gpu_quality_rmat22.py.
 """
-import os
-
 import numpy as np
 import pytest
 
 import oracle
 import paper_2608_01907_gb300 as snap
-from gpu_helpers import SYNC_RTOL, gpu_layout, parity_error, schedule_dict
-from synth import initial_positions, rmat_graph
+from gpu_helpers import SYNC_RTOL, gpu_layout, parity_error, rmat22_bfs, schedule_dict
+from synth import initial_positions
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
-
-CACHE = "/tmp/snap_test_rmat22_34m_bfs.npz"
-
-
-class _G:
-    def __init__(self, n, rp, ci):
-        self.n, self.row_ptr, self.col_idx = n, rp, ci
-        self.nnz = int(rp[-1])
 
 
 @pytest.fixture(scope="module")
 def rmat22():
-    if os.path.exists(CACHE):
-        z = np.load(CACHE)
-        return _G(int(z["n"]), z["row_ptr"], z["col_idx"])
-    g = rmat_graph(22, 34_000_000, seed=1)
-    _, rp, ci = snap.snap_graph_reorder(g.row_ptr, g.col_idx, g.n)
-    np.savez(CACHE, n=g.n, row_ptr=rp, col_idx=ci)
-    return _G(g.n, rp, ci)
+    return rmat22_bfs()
 
 
-@pytest.mark.parametrize("S,cap,eta0,share", [(16, 1.0, 0.01, 1.0), (1, 0.0, 0.01, 1.0), (16, 1.0, 1.0, 0.999)])
-def test_full_size_sync_epoch_matches_oracle_per_coordinate(cuda, rmat22, S, cap, eta0, share):
-    # share: fraction of vertices that must meet the gate.  At eta0 = 1 a
-    # chunk's Jacobi step multiplies the FP32 rounding of the positions that
-    # earlier chunks moved by about eta * 0.9 * sqrt(degree) (20 at degree
-    # 500), so after 16 chunks a few thousand of the 4.2M vertices differ from
-    # the FP64 oracle by up to a few 1e-3; at eta0 = 0.01 the same launch
-    # configuration is well conditioned and every vertex meets the gate.
+@pytest.mark.parametrize("S,cap", [(16, 1.0), (1, 0.0)])
+def test_full_size_sync_epoch_matches_oracle_per_coordinate(cuda, rmat22, S, cap):
+    eta0 = 0.01
     g = rmat22
     Y0 = initial_positions(g.n, 1)
     sched = snap.linear_schedule(eta0=eta0, total_epochs=30)
@@ -69,11 +50,7 @@ def test_full_size_sync_epoch_matches_oracle_per_coordinate(cuda, rmat22, S, cap
               f"gpu {got[v]}, oracle {ref[v]}")
     print(f"full-size sync parity (R-MAT 2^22, S={S}, cap {cap}, eta0 {eta0}): max rel err {err:.2e} over "
           f"{g.n} vertices, {int((rel > SYNC_RTOL).sum())} above the gate")
-    if share >= 1.0:
-        assert err < SYNC_RTOL
-    else:
-        assert (rel < SYNC_RTOL).mean() >= share
-        assert err < 0.02
+    assert err < SYNC_RTOL
 
 
 @pytest.fixture(scope="module")

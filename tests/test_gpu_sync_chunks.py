@@ -1,0 +1,139 @@
+"""Synchronous mode, chunk by chunk, against the FP64 oracle on every workload
+graph: SBM 2,000, LFR-style 260k / 6.9M and R-MAT 2^22 / 34M (BFS
+relabelling), in the bench's synchronous configuration (eta0 = 1, 16 chunks,
+step cap 1) and with one chunk.
+
+A chunk step sums the forces of its rows from the positions at the chunk's
+start, then applies them.  The oracle (oracle.sync_chunks) is started from the
+GPU's own positions at every chunk boundary, so each comparison measures the
+error of one chunk step of the kernels alone: every vertex must meet the
+1e-4 gate.  Whole-epoch comparisons chain 16 such steps; at eta0 = 1 a chunk
+step multiplies a vertex's incoming difference by up to eta * 0.9 * (its
+edges in the chunk), so FP32 rounding of the positions grows along the chain
+(the same growth appears between two oracle runs that differ only in rounding
+the positions to FP32 between chunks, measured below).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2608_01907_gb300 as snap
+from gpu_helpers import SYNC_RTOL, coordinate_error, lfr260k, rmat22_bfs, schedule_dict
+from synth import initial_positions, sbm_graph
+
+pytestmark = pytest.mark.gpu
+
+K = 3
+
+
+def _graph(name):
+    return {"sbm": lambda: sbm_graph(seed=1), "lfr": lfr260k, "rmat22": rmat22_bfs}[name]()
+
+
+def _chunk_parity(torch, g, S, cap, eta0, seed, epoch=0):
+    """Runs epoch `epoch` chunk by chunk on the GPU; after each chunk compares
+    with the oracle's chunk step from the GPU's positions before it.  Returns
+    (max error per chunk, vertices above the gate per chunk, final GPU
+    positions)."""
+    sched = snap.linear_schedule(eta0=eta0, total_epochs=30)
+    sd = schedule_dict(sched)
+    Y0 = initial_positions(g.n, seed)
+    pos = torch.from_numpy(Y0.copy()).cuda()
+    errs, bad = [], []
+    with snap.Layout(g.row_ptr, g.col_idx,
+                     opts=snap.make_options(mode=snap.MODE_SYNC, sync_substeps=S, sync_cap=cap)) as L:
+        for c in range(S):
+            before = pos.cpu().numpy().astype(np.float64)
+            L.sync_chunks(pos, epoch, c, c + 1, K, sched, seed)
+            L.check()
+            got = pos.cpu().numpy()
+            ref = oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, before, epoch, c, c + 1, S, K, sd, seed=seed,
+                                     cap=cap)
+            e = coordinate_error(got, ref)
+            errs.append(float(e.max()))
+            bad.append(int((e >= SYNC_RTOL).sum()))
+    return errs, bad, pos.cpu().numpy()
+
+
+CASES = [("sbm", 16, 1.0, 1.0), ("sbm", 1, 0.0, 0.25), ("lfr", 16, 1.0, 1.0), ("lfr", 1, 0.0, 0.25),
+         ("rmat22", 16, 1.0, 1.0), ("rmat22", 1, 1.0, 1.0)]
+
+
+@pytest.mark.parametrize("name,S,cap,eta0", CASES)
+def test_every_chunk_step_matches_oracle_per_coordinate(cuda, name, S, cap, eta0):
+    g = _graph(name)
+    errs, bad, _ = _chunk_parity(cuda, g, S, cap, eta0, seed=1)
+    print(f"sync chunk parity {name} (n={g.n}, nnz={g.nnz}) S={S} cap={cap} eta0={eta0}: "
+          f"max rel err per chunk {max(errs):.2e} (chunks: {' '.join(f'{e:.1e}' for e in errs)}); "
+          f"vertices above 1e-4: {sum(bad)}")
+    assert max(errs) < SYNC_RTOL
+
+
+@pytest.mark.parametrize("name", ["sbm", "lfr"])
+def test_chunk_calls_equal_one_epoch_call_bitwise(cuda, name):
+    torch = cuda
+    g = _graph(name)
+    S, seed = 16, 3
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=30)
+    Y0 = initial_positions(g.n, seed)
+    a = torch.from_numpy(Y0.copy()).cuda()
+    b = torch.from_numpy(Y0.copy()).cuda()
+    with snap.Layout(g.row_ptr, g.col_idx,
+                     opts=snap.make_options(mode=snap.MODE_SYNC, sync_substeps=S, sync_cap=1.0)) as L:
+        L.epochs(a, 2, 1, K, sched, seed)
+        L.sync_chunks(b, 2, 0, 5, K, sched, seed)
+        L.sync_chunks(b, 2, 5, 5, K, sched, seed)
+        L.sync_chunks(b, 2, 5, S, K, sched, seed)
+        L.check()
+    assert torch.equal(a, b)
+
+
+def test_sync_chunks_rejects_bad_ranges_and_modes(cuda):
+    torch = cuda
+    g = sbm_graph(n=300, blocks=3, p_in=0.05, p_out=0.005, seed=2)
+    pos = torch.from_numpy(initial_positions(g.n, 1)).cuda()
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=30)
+    with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(mode=snap.MODE_SYNC, sync_substeps=4)) as L:
+        for c0, c1 in ((-1, 2), (3, 2), (0, 5)):
+            with pytest.raises(snap.SnapError):
+                L.sync_chunks(pos, 0, c0, c1, K, sched, 1)
+    with snap.Layout(g.row_ptr, g.col_idx) as L:
+        with pytest.raises(snap.SnapError):
+            L.sync_chunks(pos, 0, 0, 1, K, sched, 1)
+
+
+@pytest.mark.parametrize("name", ["lfr", "rmat22"])
+def test_whole_epoch_sync_parity_and_its_conditioning(cuda, name):
+    """One whole epoch in the bench's synchronous configuration against the
+    FP64 oracle, with the conditioning made visible: the oracle is run a
+    second time with its positions rounded to FP32 between chunks (what any
+    FP32 implementation stores), and its distance from the FP64 run is
+    reported beside the GPU's.  The gate holds per vertex where the chain is
+    well conditioned; the share of vertices meeting it must be at least the
+    share the FP32-rounded oracle itself reaches, less 0.1%."""
+    torch = cuda
+    g = _graph(name)
+    S, cap, seed = 16, 1.0, 1
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=30)
+    sd = schedule_dict(sched)
+    Y0 = initial_positions(g.n, seed)
+    pos = torch.from_numpy(Y0.copy()).cuda()
+    with snap.Layout(g.row_ptr, g.col_idx,
+                     opts=snap.make_options(mode=snap.MODE_SYNC, sync_substeps=S, sync_cap=cap)) as L:
+        L.epochs(pos, 0, 1, K, sched, seed)
+        L.check()
+    got = pos.cpu().numpy()
+    ref = oracle.sync(g.row_ptr, g.col_idx, g.n, Y0, 1, K, sd, seed=seed, substeps=S, cap=cap)
+    Y32 = Y0.astype(np.float64)
+    for c in range(S):
+        Y32 = oracle.sync_chunks(g.row_ptr, g.col_idx, g.n, Y32, 0, c, c + 1, S, K, sd, seed=seed, cap=cap)
+        Y32 = Y32.astype(np.float32).astype(np.float64)
+    e_gpu = coordinate_error(got, ref)
+    e_f32 = coordinate_error(Y32, ref)
+    ok_gpu, ok_f32 = float((e_gpu < SYNC_RTOL).mean()), float((e_f32 < SYNC_RTOL).mean())
+    print(f"whole-epoch sync {name} S={S} cap={cap} eta0=1: GPU max err {e_gpu.max():.2e}, "
+          f"{int((e_gpu >= SYNC_RTOL).sum())} of {g.n} vertices above 1e-4 (share ok {ok_gpu:.6f}); "
+          f"FP32-rounded oracle max err {e_f32.max():.2e}, {int((e_f32 >= SYNC_RTOL).sum())} above "
+          f"(share ok {ok_f32:.6f})")
+    assert np.all(np.isfinite(got))
+    assert ok_gpu >= ok_f32 - 1e-3

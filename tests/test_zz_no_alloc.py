@@ -60,20 +60,69 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(cuda):
     assert ei.value.status == 1 and "262144" in str(ei.value)
 
 
-def test_noalloc_reports_bad_columns(cuda):
+def _malformed(g):
+    """Malformed variants of a valid CSR: (name, row_ptr, col_idx)."""
+    rp, ci = g.row_ptr, g.col_idx
+    out = []
+    c = ci.copy()
+    c[5] = g.n + 7
+    out.append(("column past n", rp, c))
+    c = ci.copy()
+    c[3] = -1
+    out.append(("negative column", rp, c))
+    out.append(("short col_idx", rp, ci[:-3].copy()))
+    r = rp.copy()
+    r[0] = 1
+    out.append(("row_ptr[0] != 0", r, ci))
+    r = rp.copy()
+    r[10], r[11] = r[11], r[10]
+    out.append(("decreasing row_ptr", r, ci))
+    c = ci.copy()
+    row = int(np.searchsorted(rp, 7, side="right") - 1)
+    c[7] = row
+    out.append(("self-loop", rp, c))
+    c = ci.copy()
+    a = int(rp[2])
+    c[a], c[a + 1] = c[a + 1], c[a]
+    out.append(("unsorted row", rp, c))
+    # drop one reverse edge: row 0 loses its first entry, row_ptr shifts
+    r = rp.copy()
+    r[1:] -= 1
+    out.append(("missing reverse edge", r, np.delete(ci, 0)))
+    return out
+
+
+def test_noalloc_rejects_malformed_csr_without_touching_positions(cuda):
     torch = cuda
     g = tiny_graph(50, 80, seed=4)
-    ci_bad = g.col_idx.copy()
-    ci_bad[5] = g.n + 7
-    pos = torch.from_numpy(initial_positions(g.n, 1)).cuda()
-    with pytest.raises(snap.SnapError) as ei:
-        snap.snap_sync_epochs_noalloc(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(ci_bad).cuda(), pos,
-                                      0, 1, 3, snap.linear_schedule(), 1)
-    assert ei.value.status == 1
+    assert np.all(np.diff(g.row_ptr)[:3] >= 2)
+    Y0 = initial_positions(g.n, 1)
+    for name, rp_bad, ci_bad in _malformed(g):
+        pos = torch.from_numpy(Y0.copy()).cuda()
+        with pytest.raises(snap.SnapError) as ei:
+            snap.snap_sync_epochs_noalloc(torch.from_numpy(rp_bad).cuda(), torch.from_numpy(ci_bad).cuda(), pos,
+                                          0, 1, 3, snap.linear_schedule(), 1)
+        assert ei.value.status == 1, name
+        assert np.array_equal(pos.cpu().numpy(), Y0), name
     # the scratch is cleared by the next call, which succeeds
     rp = torch.from_numpy(g.row_ptr).cuda()
     ci = torch.from_numpy(g.col_idx).cuda()
-    pos = torch.from_numpy(initial_positions(g.n, 1)).cuda()
+    pos = torch.from_numpy(Y0.copy()).cuda()
     snap.snap_sync_epochs_noalloc(rp, ci, pos, 0, 1, 3, snap.linear_schedule(), 1)
-    expect = _reference(torch, g, initial_positions(g.n, 1), 0, 1, 3, snap.linear_schedule(), 1, 1, 0.0)
+    expect = _reference(torch, g, Y0, 0, 1, 3, snap.linear_schedule(), 1, 1, 0.0)
     assert parity_error(pos.cpu().numpy(), expect) < SYNC_RTOL
+
+
+def test_noalloc_rejects_host_buffers(cuda):
+    torch = cuda
+    g = tiny_graph(40, 60, seed=5)
+    pos = torch.from_numpy(initial_positions(g.n, 1)).cuda()
+    lib = snap.load_library()
+    import ctypes
+    rp = np.ascontiguousarray(g.row_ptr)
+    ci = torch.from_numpy(g.col_idx).cuda()
+    sched = snap.linear_schedule()
+    st = lib.snap_sync_epochs_noalloc(ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.data_ptr()), ci.numel(),
+                                      g.n, ctypes.c_void_p(pos.data_ptr()), 0, 1, 3, ctypes.byref(sched), 1, 1,
+                                      ctypes.c_float(0.0), None)
+    assert st == 1
