@@ -58,7 +58,13 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--cpu-sample-edges", type=int, default=12_000_000)
+    p.add_argument("--no-probe", action="store_true")
+    p.add_argument("--no-batch-serve", action="store_true",
+                   help="skip the batch and serve sub-objects of the default line")
+    p.add_argument("--cpu-sample-edges", type=int, default=12_000_000,
+                   help="directed edges of the oracle's sampled epoch (the cpu_baseline leg)")
+    p.add_argument("--ref-sample-edges", type=int, default=3_000_000,
+                   help="directed edges of the oracle's sampled epoch per step of --impl reference")
     p.add_argument("--workload", default="rmat", choices=["rmat", "batch", "serve"],
                    help="rmat: the 4M/34M headline; batch: many small SBM graphs, batched vs one launch per "
                         "graph; serve: Poisson layout requests, continuous batching vs one job at a time")
@@ -70,26 +76,85 @@ def parse():
 
 
 def load_graph(scale, edges, seed, generator="numpy"):
-    """R-MAT graph relabelled by snap_graph_reorder; cached on local disk
-    (numpy generator only: the native one regenerates faster than a reload)."""
-    import paper_2608_01907_gb300 as snap
+    """R-MAT graph relabelled by the input generators' breadth-first locality
+    relabelling (synth.bfs_relabel, the same labels as the library's
+    snap_graph_reorder); cached on local disk under a key that includes the
+    hash of the generator sources (numpy generator only: the native one
+    regenerates faster than a reload)."""
+    from synth import bfs_relabel, source_digest
     if generator == "native":
         from synth import rmat_graph_native
-        g = rmat_graph_native(scale, edges, seed=seed)
-        _, rp, ci = snap.snap_graph_reorder(g.row_ptr, g.col_idx, g.n)
-        return g.n, rp, ci
+        g = bfs_relabel(rmat_graph_native(scale, edges, seed=seed))
+        return g.n, g.row_ptr, g.col_idx
     cache = os.path.join(tempfile.gettempdir(), "snap_bench_cache")
     os.makedirs(cache, exist_ok=True)
-    path = os.path.join(cache, f"rmat{scale}_{edges}_s{seed}_bfs.npz")
+    path = os.path.join(cache, f"rmat{scale}_{edges}_s{seed}_bfs_{source_digest()}.npz")
     if os.path.exists(path):
         z = np.load(path)
         return int(z["n"]), z["row_ptr"], z["col_idx"]
-    g = rmat_graph(scale=scale, num_edges=edges, seed=seed)
-    _, rp, ci = snap.snap_graph_reorder(g.row_ptr, g.col_idx, g.n)
+    g = bfs_relabel(rmat_graph(scale=scale, num_edges=edges, seed=seed))
     tmp = path + f".{os.getpid()}.npz"
-    np.savez(tmp, n=g.n, row_ptr=rp, col_idx=ci)
+    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col_idx=g.col_idx)
     os.replace(tmp, path)
-    return g.n, rp, ci
+    return g.n, g.row_ptr, g.col_idx
+
+
+def workload_config(args, n, nnz, isolated):
+    """The config object both arms print (the same keys and values)."""
+    return {"workload": f"rmat{args.scale}-{args.edges}e-k{args.k}-{EPOCHS}ep-bfs"
+                        + ("-native" if args.generator == "native" else ""),
+            "n": n, "undirected_edges": args.edges, "directed_edges": nnz, "k": args.k, "epochs": EPOCHS,
+            "mode": args.mode, "sampler": args.sampler, "isolated_nodes": isolated,
+            "l2": "inputs larger than L2 on the device: the entry stream (16 B per undirected edge) is re-read from "
+                  "HBM every epoch; the positions (8 B per vertex) stay L2-resident when they fit"}
+
+
+PROBE_SRC = os.path.join(ROOT, "bench_probe.cu")
+PROBE_LIB = os.path.join(ROOT, "libbench_probe.so")
+
+
+def probe_library():
+    """The hardware probe (bench_probe.cu), compiled for sm_103a on first use."""
+    import ctypes
+    import shutil
+    if not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_LIB) < os.path.getmtime(PROBE_SRC):
+        nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = PROBE_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                               "-Xcompiler", "-fPIC", "-shared", "-cudart", "static", PROBE_SRC, "-o", tmp])
+        os.replace(tmp, PROBE_LIB)
+    lib = ctypes.CDLL(PROBE_LIB)
+    lib.bench_probe_rate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    lib.bench_probe_rate.restype = ctypes.c_double
+    return lib
+
+
+def probe_rates(nbytes, stream):
+    """Hardware ceilings measured now on an array of `nbytes` (the size of the
+    position array): L2 streaming read bandwidth (bytes/s; the array fits in
+    L2), random 8-byte loads/s and random 8-byte vector atomic adds/s, each
+    alone (bench_probe.cu).  Best of two runs each."""
+    import ctypes
+    import torch
+    lib = probe_library()
+    nbytes = max(32, (int(nbytes) + 15) // 16 * 16)
+    buf = torch.zeros(nbytes // 4, dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sms = torch.cuda.get_device_properties(buf.device).multi_processor_count
+    out = {}
+    for name, op, iters, grid in (("l2_read_bytes_per_s", 0, 16, sms * 8), ("random_loads_per_s", 1, 16, sms * 8),
+                                  ("random_atomic_adds_per_s", 2, 16, sms * 8)):
+        best = 0.0
+        for _ in range(2):
+            r = lib.bench_probe_rate(ctypes.c_void_p(buf.data_ptr()), nbytes, op, iters, grid,
+                                     ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+            if r < 0:
+                raise RuntimeError(f"bench_probe_rate op {op} failed ({r})")
+            best = max(best, r)
+        out[name] = best
+    del buf, sink
+    return out
 
 
 def measured_peak():
@@ -223,6 +288,82 @@ def cpu_baseline(n, row_ptr, col_idx, Y0, k, sample_edges, seed, sampler="unifor
             "seconds": work}
 
 
+def rooflines(nnz, n, k, launch_ms, probes, peak_hbm, peak_kind, traffic, kernel, sync=False):
+    """Rooflines of one epoch launch from algorithmic counts per launch.
+
+    HBM term: the edge stream, 4 B per directed edge (its column) plus 8 B of
+    row offsets per vertex, against the measured HBM copy bandwidth.
+    L2 term: every directed edge reads and writes the position of its partner
+    and of its k negatives, (k+1) reads and (k+1) writes of 8 B, each one
+    32-byte L2 sector (64 (k+1) B per directed edge; the synchronous mode's
+    write is two 8-byte integer atomics, 96 (k+1) B), against the L2
+    streaming-read bandwidth measured in this run.
+    Operation term: the same (k+1) random loads and (k+1) random atomic adds
+    per directed edge against the rates the probes measured for random 8-byte
+    loads alone and random 8-byte vector atomic adds alone; the bound is the
+    larger of the two times.
+    The binding roofline is the larger of the HBM and L2 times."""
+    launch_s = launch_ms / 1e3
+    hbm_bytes = 4 * nnz + 8 * (n + 1)
+    l2_bytes = (96 if sync else 64) * (k + 1) * nnz
+    hbm = {"bound": "hbm", "achieved": hbm_bytes / launch_s / 1e9, "peak": peak_hbm, "unit": "GB/s",
+           "frac": hbm_bytes / launch_s / 1e9 / peak_hbm, "traffic": traffic,
+           "traffic_over_algorithmic": (traffic / hbm_bytes) if traffic else None,
+           "algorithmic_bytes_per_launch": hbm_bytes, "avg_launch_ms": launch_ms, "kernel": kernel,
+           "peak_source": f"{peak_kind} hbm_gbs (copy), of {peak_kind}",
+           "per_unit": "4 B per directed edge + 8 B per vertex"}
+    l2 = ops = None
+    if probes:
+        l2_peak = probes["l2_read_bytes_per_s"] / 1e9
+        l2 = {"bound": "l2", "achieved": l2_bytes / launch_s / 1e9, "peak": l2_peak, "unit": "GB/s",
+              "frac": l2_bytes / launch_s / 1e9 / l2_peak, "traffic": traffic,
+              "algorithmic_bytes_per_launch": l2_bytes, "avg_launch_ms": launch_ms, "kernel": kernel,
+              "peak_source": "L2 streaming read measured in this run (bench_probe.cu op 0, 16-B coalesced loads "
+                             "sweeping an L2-resident array the size of the positions), of measured",
+              "per_unit": f"{96 if sync else 64} (k+1) B per directed edge (32-B sectors)"}
+        n_ops = (k + 1) * nnz
+        t_load = n_ops / probes["random_loads_per_s"]
+        t_add = (2 if sync else 1) * n_ops / probes["random_atomic_adds_per_s"]
+        t_bound = max(t_load, t_add)
+        ops = {"loads_per_launch": n_ops, "atomic_adds_per_launch": (2 if sync else 1) * n_ops,
+               "load_peak_per_s": probes["random_loads_per_s"],
+               "atomic_add_peak_per_s": probes["random_atomic_adds_per_s"],
+               "bound_ms": t_bound * 1e3, "frac": t_bound / launch_s,
+               "binding": "atomic adds" if t_add >= t_load else "loads",
+               "note": "random 8-byte loads and vector float atomic adds, each probed alone (bench_probe.cu ops 1-2)"}
+    binding = hbm
+    if l2 and l2_bytes / (l2["peak"] * 1e9) > hbm_bytes / (peak_hbm * 1e9):
+        binding = l2
+    return {"binding": binding, "hbm": hbm, "l2": l2, "ops": ops}
+
+
+def cpu_hogwild_baseline(n, row_ptr, col_idx, Y0, k, seed, epochs=2):
+    """The multi-threaded FP32 CPU Hogwild (oracle/cpu_hogwild.c, the paper's
+    bundle scheme): whole epochs of the same graph on all host cores and on
+    16 threads, after one untimed epoch."""
+    import oracle
+    sched = dict(kind=0, eta0=1.0, eta_min=1e-3, total_epochs=EPOCHS)
+    nnz = int(row_ptr[-1])
+    cores = os.cpu_count() or 1
+    out = {"kind": "cpu_hogwild_fp32", "unit": UNIT, "host": host_info()}
+    for label, threads in (("all_cores", cores), ("threads16", 16)):
+        if label == "threads16" and threads == cores:
+            out[label] = out["all_cores"]
+            continue
+        Y, used = oracle.cpu_hogwild(row_ptr, col_idx, n, Y0, 1, k, sched, seed=seed, threads=threads)
+        t0 = time.perf_counter()
+        Y, used = oracle.cpu_hogwild(row_ptr, col_idx, n, Y, epochs, k, sched, seed=seed, threads=threads,
+                                     epoch_begin=1)
+        dt = time.perf_counter() - t0
+        out[label] = {"value": epochs * nnz * (1 + k) / dt, "cores": used, "seconds": dt,
+                      "sample": f"{epochs} whole epochs of the workload graph after one untimed epoch, FP32, "
+                                f"{used} OpenMP threads, bundles (a source's out-edges) in a random order"}
+    out["value"] = out["all_cores"]["value"]
+    out["cores"] = out["all_cores"]["cores"]
+    out["sample"] = out["all_cores"]["sample"]
+    return out
+
+
 def replica_throughput(local_ms: float, units_per_rank: float, dist=None, device=None):
     """Whole-job throughput of N independent replicas: the units all ranks
     processed divided by the slowest rank's time (max over ranks).
@@ -247,7 +388,7 @@ def run_reference(args, rank, world):
     oracle.build()
     sched = dict(kind=0, eta0=1.0, eta_min=1e-3, total_epochs=EPOCHS)
     sam = oracle_sampler(args.sampler, row_ptr)
-    M = args.cpu_sample_edges
+    M = args.ref_sample_edges
     t0 = time.perf_counter()
     oracle.seq(row_ptr, col_idx, n, Y0, 0, args.k, sched, seed=args.seed)
     t_shuffle = time.perf_counter() - t0
@@ -266,8 +407,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "s_per_layout_extrapolated": per_layout,
-            "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{args.k}-{EPOCHS}ep-bfs", "n": n,
-                       "undirected_edges": args.edges, "k": args.k, "epochs": EPOCHS, "sampler": args.sampler},
+            "config": workload_config(args, n, int(row_ptr[-1]), int((np.diff(row_ptr) == 0).sum())),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"each step: 1 epoch limited to {done} of {int(row_ptr[-1])} directed "
                                        f"edges, FP64 Algorithm 1, "
@@ -391,41 +531,15 @@ def run_snap(args, rank, world, local_rank):
         snap.snap_layout_destroy(h3)
         extras["k_sweep"] = sweep
 
-    # ceiling of the access pattern that binds the epoch kernel: random
-    # dependent read-modify-writes of 8-byte slots in an L2-resident array
-    # of the same size as the positions, measured now by the probe kernel
-    rmw_peak = None
-    if not args.no_extras:
-        from paper_2608_01907_gb300 import probe
-        scratch = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
-        # the write each mode issues after its read: an atomic add (HOGWILD_RED) or an exchange (HOGWILD)
-        op = "load_dep_atomic" if mode == snap.MODE_HOGWILD_RED else "load_exch"
-        rmw_peak = max(probe.random_access_rate(scratch, op, depth=d, iters=32) for d in (1, 4))
-        del scratch
-
-    # roofline of the epoch kernel: algorithmic bytes per launch
+    # hardware ceilings measured now, on an array the size of the positions
+    probes = probe_rates(8 * n, stream) if not args.no_probe else None
+    peak, peak_kind = measured_peak()
+    kname = (f"oriented_epoch_kernel<RED={int(mode == snap.MODE_HOGWILD_RED)},G={min(k, 4)}>"
+             if mode != snap.MODE_SYNC else "sync epoch (sync_chunk_kernel + sync_apply_kernel)")
+    roofs = rooflines(nnz, n, k, float(np.mean(launch_ms)), probes, peak, peak_kind,
+                      recorded_traffic(args.mode, k), kname, sync=mode == snap.MODE_SYNC)
     deg = np.diff(row_ptr)
     nonempty = int((deg > 0).sum())
-    alg_bytes = nnz * (4 + 16 * (1 + k)) + 8 * (n + 1) + 16 * nonempty
-    peak, peak_kind = measured_peak()
-    achieved = alg_bytes / (float(np.mean(launch_ms)) / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(args.mode, k),
-            "kernel": (f"oriented_epoch_kernel<RED={int(mode == snap.MODE_HOGWILD_RED)},G={min(k, 4)}>"
-                       if mode != snap.MODE_SYNC else "sync epoch (sync_chunk_kernel + sync_apply_kernel)"),
-            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": float(np.mean(launch_ms)),
-            "peak_source": f"{peak_kind} hbm_gbs (copy)"}
-    roof_l2 = None
-    if rmw_peak and mode != snap.MODE_SYNC:
-        # per undirected edge the oriented kernel read-modify-writes the
-        # partner once and 2k negatives once each
-        rmw_per_launch = (nnz // 2) * (1 + 2 * k)
-        ach = rmw_per_launch / (float(np.mean(launch_ms)) / 1e3)
-        roof_l2 = {"bound": "l2 dependent read-modify-write (random 8-byte slots)", "achieved": ach / 1e9,
-                   "peak": rmw_peak / 1e9, "unit": "G RMW/s", "frac": ach / rmw_peak,
-                   "rmw_per_launch": rmw_per_launch,
-                   "peak_source": "probe kernel (csrc/probe_l2.cu) measured in this run on an L2-resident array "
-                                  "of n float2 slots"}
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -449,32 +563,29 @@ def run_snap(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(y_np.nbytes), "s_per_layout": e2e_s,
                "includes": "create (H2D CSR, device validation, tables), H2D positions, 30 epochs, D2H positions"}
 
-    cpu = None
+    cpu = cpu_hog = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, row_ptr, col_idx, Y0.astype(np.float64), k, args.cpu_sample_edges, args.seed,
                            args.sampler)
+        if args.sampler == "uniform":
+            cpu_hog = cpu_hogwild_baseline(n, row_ptr, col_idx, Y0, k, args.seed)
 
-    l2_bytes = getattr(torch.cuda.get_device_properties(local_rank), "L2_cache_size", 126 << 20)
-    pos_mb, stream_mb = 8 * n / 1e6, 16 * (nnz // 2) / 1e6
-    l2_note = ((f"inputs larger than L2 ({l2_bytes / 1e6:.0f} MB): the {stream_mb:.0f} MB entry stream is re-read "
-                if stream_mb * 1e6 > l2_bytes else
-                f"inputs smaller than L2 ({l2_bytes / 1e6:.0f} MB) and not flushed: the {stream_mb:.0f} MB entry "
-                f"stream is re-read ")
-               + f"every epoch; the {pos_mb:.1f} MB positions "
-               + ("stay L2-resident by design" if 8 * n < l2_bytes // 2 else "exceed L2 (random gathers reach HBM)"))
+    batch = serve = None
+    if rank == 0 and world == 1 and not args.no_extras and not args.no_batch_serve:
+        torch.cuda.synchronize()
+        batch = batch_result(args, local_rank, steps=3, warmup=3)
+        serve = serve_result(args, local_rank, seconds=min(args.serve_seconds, 3.0))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_layout": ms_per_step / 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"rmat{args.scale}-{args.edges}e-k{k}-{EPOCHS}ep-bfs"
-                               + ("-native" if args.generator == "native" else ""), "n": n,
-                           "undirected_edges": args.edges, "directed_edges": nnz, "k": k, "epochs": EPOCHS,
-                           "mode": args.mode, "sampler": args.sampler, "isolated_nodes": int(n - nonempty),
-                           "l2": l2_note,
-                           "parallelism": f"replicas x{world}"},
-                "roofline": roof, "roofline_l2": roof_l2, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * EPOCHS * launches_per_epoch, "clocks": clk}
+                "config": dict(workload_config(args, n, nnz, int(n - nonempty)), parallelism=f"replicas x{world}"),
+                "roofline": roofs["binding"], "roofline_hbm": roofs["hbm"], "roofline_l2": roofs["l2"],
+                "l2_ops": roofs["ops"], "probes": probes, "cpu_baseline": cpu, "cpu_baseline_hogwild": cpu_hog,
+                "e2e": e2e, "gpu_launches": args.steps * EPOCHS * launches_per_epoch, "clocks": clk,
+                "batch": batch, "serve": serve}
         line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -488,7 +599,8 @@ def load_batch(count, seed):
     from synth import batch_sbm_graphs
     cache = os.path.join(tempfile.gettempdir(), "snap_bench_cache")
     os.makedirs(cache, exist_ok=True)
-    path = os.path.join(cache, f"batch_sbm_{count}_s{seed}.npz")
+    from synth import source_digest
+    path = os.path.join(cache, f"batch_sbm_{count}_s{seed}_{source_digest()}.npz")
     if os.path.exists(path):
         z = np.load(path)
         return z["row_ptr"], z["col_idx"], z["offsets"]
@@ -500,10 +612,10 @@ def load_batch(count, seed):
     return rp, ci, offs
 
 
-def run_batch(args, rank, world, local_rank):
+def batch_result(args, local_rank, steps, warmup):
     """Config 4: many small graphs in one handle against one handle (and one
     launch per epoch) per graph.  One step = the 30-epoch layout of all
-    graphs."""
+    graphs.  Returns the result object."""
     import torch
     import paper_2608_01907_gb300 as snap
     torch.cuda.set_device(local_rank)
@@ -527,7 +639,7 @@ def run_batch(args, rank, world, local_rank):
         Y.copy_(Y0_d)
         snap.snap_layout_epochs(h, Y, 0, EPOCHS, k, sched, args.seed, stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     snap.snap_layout_check(h, stream)
     torch.cuda.synchronize()
@@ -535,38 +647,21 @@ def run_batch(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     snap.snap_layout_check(h, stream)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     updates = EPOCHS * nnz * (1 + k)
     snap.snap_layout_destroy(h)
 
-    # rooflines of one epoch launch, as for the single graph: algorithmic
-    # bytes against the HBM copy peak, and the launch's dependent random
-    # read + atomic adds against the probe's ceiling on an array of n slots
-    deg = np.diff(rp)
-    alg_bytes = nnz * (4 + 16 * (1 + k)) + 8 * (n + 1) + 16 * int((deg > 0).sum())
-    launch_s = ms / 1e3 / EPOCHS
+    launch_ms = ms / EPOCHS
     peak, peak_kind = measured_peak()
-    roof = {"bound": "hbm", "achieved": alg_bytes / launch_s / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": alg_bytes / launch_s / 1e9 / peak, "traffic": None,
-            "kernel": f"oriented_epoch_kernel<RED=1,G={min(k, 4)},MULTI=1>",
-            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": launch_s * 1e3,
-            "launch_time": "30-epoch CUDA-graph replay (CUDA events on the stream) / 30",
-            "peak_source": f"{peak_kind} hbm_gbs (copy)"}
-    from paper_2608_01907_gb300 import probe
-    scratch = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
-    rmw_peak = max(probe.random_access_rate(scratch, "load_dep_atomic", depth=d, iters=32) for d in (1, 4))
-    del scratch
-    rmw_per_launch = (nnz // 2) * (1 + 2 * k)
-    roof_l2 = {"bound": "l2 dependent read-modify-write (random 8-byte slots)",
-               "achieved": rmw_per_launch / launch_s / 1e9, "peak": rmw_peak / 1e9, "unit": "G RMW/s",
-               "frac": rmw_per_launch / launch_s / rmw_peak, "rmw_per_launch": rmw_per_launch,
-               "peak_source": "probe kernel (csrc/probe_l2.cu) measured in this run on n float2 slots"}
+    probes = probe_rates(8 * n, stream) if not args.no_probe else None
+    roofs = rooflines(nnz, n, k, launch_ms, probes, peak, peak_kind, None,
+                      f"oriented_epoch_kernel<RED=1,G={min(k, 4)},MULTI=1>")
 
     # one graph per handle and per launch, on a seeded sample of the graphs
     rng = np.random.default_rng(args.seed)
@@ -593,9 +688,8 @@ def run_batch(args, rank, world, local_rank):
     upd_pg = EPOCHS * sum(m for _, _, m, _ in handles) * (1 + k)
     for _, _, _, hh in handles:
         snap.snap_layout_destroy(hh)
-    line = {"metric": "batched layouts: pair updates/s and s per batch (30 epochs)", "value": updates / (ms / 1e3),
-            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {"metric": "batched layouts: pair updates/s and s per batch (30 epochs)", "value": updates / (ms / 1e3),
+            "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "config": {"workload": f"batch-sbm-{offs.size - 1}-graphs-k{k}-{EPOCHS}ep", "graphs": int(offs.size - 1),
                        "n_total": n, "undirected_edges": nnz // 2, "mode": "hogwild_red",
                        "autotuned": {"chunk_entries": seg, "block": blk, "ms_per_epoch": tune_ms,
@@ -606,19 +700,25 @@ def run_batch(args, rank, world, local_rank):
             "one_graph_per_launch": {"updates_per_s": upd_pg / (ms_pg / 1e3), "graphs_timed": len(handles),
                                      "launches": len(handles) * EPOCHS, "ms": ms_pg},
             "speedup_vs_one_graph_per_launch": (updates / (ms / 1e3)) / (upd_pg / (ms_pg / 1e3)),
-            "roofline": roof, "roofline_l2": roof_l2,
-            "gpu_launches": args.steps * EPOCHS, "clocks": clk}
+            "roofline": roofs["binding"], "roofline_hbm": roofs["hbm"], "roofline_l2": roofs["l2"],
+            "l2_ops": roofs["ops"], "gpu_launches": steps * EPOCHS, "clocks": clk}
+
+
+def run_batch(args, rank, world, local_rank):
+    line = batch_result(args, local_rank, args.steps, args.warmup)
+    line.update({"n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                 "data": "synthetic"})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_serve(args, rank, world, local_rank):
+def serve_result(args, local_rank, seconds):
     """Config 5: layout requests arriving as a Poisson stream (mean 200/s) over
     R-MAT and planted-partition graphs with |E| log-uniform in [1k, 2M];
     continuous batching (LayoutServer) against the plain loop (one job at a
-    time, first come first served) on the same arrival schedule."""
+    time, first come first served) on the same arrival schedule.  Returns the
+    result object."""
     import torch
-    import paper_2608_01907_gb300 as snap
     from paper_2608_01907_gb300.serve import Job, LayoutServer, run_sequential
     from synth import serving_graph_pool
     torch.cuda.set_device(local_rank)
@@ -628,7 +728,7 @@ def run_serve(args, rank, world, local_rank):
     t = 0.0
     while True:
         t += rng.exponential(1.0 / args.serve_rate)
-        if t > args.serve_seconds:
+        if t > seconds:
             break
         arrivals.append(t)
     picks = rng.integers(0, len(pool), len(arrivals))
@@ -686,18 +786,25 @@ def run_serve(args, rank, world, local_rank):
 
     srv, seq = summary(jobs_s, t0_s), summary(jobs_p, t0_p)
     finite = all(np.all(np.isfinite(j.positions)) for j in jobs_s)
-    line = {"metric": "served layout requests: p50/p99 latency and pair updates/s", "value": srv["updates_per_s"],
-            "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    return {"metric": "served layout requests: p50/p99 latency and pair updates/s", "value": srv["updates_per_s"],
+            "unit": UNIT, "steps": 1, "warmup": 1,
             "config": {"workload": f"serve-poisson{args.serve_rate:g}-{len(arrivals)}jobs-{EPOCHS}ep-k{k}",
-                       "jobs": len(arrivals), "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+                       "jobs": len(arrivals), "rate_per_s": args.serve_rate, "seconds": seconds,
                        "graph_pool": "48 graphs: R-MAT / 8-community planted partition, |E| log-uniform 1k-2M",
                        "mode": "hogwild_red",
+                       "admission": "peak preparation bytes within the budget (half the free HBM at start) and "
+                                    "within the driver-reported free memory; reservation = handle bytes + positions",
                        "l2": "not flushed: a job's entries (<= 32 MB) and positions may stay in L2 across its "
                              "epochs, as they would in any server"},
             "continuous_batching": srv, "one_job_at_a_time": seq,
             "p99_speedup": seq["p99_s"] / srv["p99_s"], "throughput_ratio": srv["updates_per_s"] / seq["updates_per_s"],
             "all_finite": finite, "clocks": clk}
+
+
+def run_serve(args, rank, world, local_rank):
+    line = serve_result(args, local_rank, args.serve_seconds)
+    line.update({"n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                 "data": "synthetic"})
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -1,5 +1,8 @@
 """FP64 sequential CPU oracle for SNAP-tFDP -- TEST INFRASTRUCTURE ONLY.
 
+(Also the bench's multi-threaded FP32 CPU baseline, ``cpu_hogwild``, from
+``cpu_hogwild.c``: the paper's lock-free bundle scheme of Section 3.4.)
+
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never calls it and
 shares no code with it: the C source ``snap_oracle.c`` restates every formula
@@ -64,15 +67,49 @@ BETA = 8.0
 GAMMA = 2.0
 
 
+_HOG_SRC = os.path.join(_HERE, "cpu_hogwild.c")
+_HOG_LIB = os.path.join(_HERE, "libcpu_hogwild.so")
+_hog = None
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, no fused multiply-add)."""
+    """Compile the oracle with gcc (plain C11, no fused multiply-add), and the
+    multi-threaded CPU Hogwild baseline (-O3, OpenMP)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
+    if force or not os.path.exists(_HOG_LIB) or os.path.getmtime(_HOG_LIB) < os.path.getmtime(_HOG_SRC):
+        tmp = _HOG_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _HOG_SRC])
+        os.replace(tmp, _HOG_LIB)
     return _LIB
+
+
+def cpu_hogwild(row_ptr, col_idx, n, Y0, epochs, k, schedule=None, seed=1, threads=0, epoch_begin=0,
+                bundle_order=None, order_seed=7):
+    """The CPU baseline (cpu_hogwild.c): FP32 lock-free epochs of Algorithm 1
+    with one bundle (a source's out-edges) per thread at a time, bundles in a
+    seeded random order.  Returns (positions float32 (n,2), threads used)."""
+    global _hog
+    if _hog is None:
+        build()
+        lib = ctypes.CDLL(_HOG_LIB)
+        P, i32, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+        lib.cpu_hogwild_epochs.argtypes = [P, P, i32, P, i32, i32, i32, i32, f64, f64, i32, u64, i32, P]
+        lib.cpu_hogwild_epochs.restype = ctypes.c_int
+        _hog = lib
+    rp, ci = _csr(row_ptr, col_idx)
+    Y = np.ascontiguousarray(Y0, dtype=np.float32).copy()
+    if bundle_order is None:
+        bundle_order = np.random.default_rng(order_seed).permutation(n)
+    order = np.ascontiguousarray(bundle_order, dtype=np.int32)
+    kind, eta0, eta_min, total = _sched(schedule)
+    used = _hog.cpu_hogwild_epochs(_p(rp), _p(ci), n, _p(Y), epoch_begin, epochs, k, kind, eta0, eta_min, total,
+                                   seed, threads, _p(order))
+    return Y, used
 
 
 def _load():

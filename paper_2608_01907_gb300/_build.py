@@ -15,7 +15,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsnap_layout.so")
-PROBE_LIB = os.path.join(HERE, "libsnap_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["capi.cu", "epoch_kernels.cu", "epoch_weighted.cu", "epoch_energy.cu", "graph_kernels.cu",
               "sync_noalloc.cu"]
@@ -36,9 +35,9 @@ def _sources() -> list[str]:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
+    if not os.path.exists(LIB):
         return False
-    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
+    t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _sources())
 
 
@@ -54,9 +53,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
         jobs.append([nvcc, *ARCH, *extra, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xptxas", "-v" if verbose else "-O3",
                      "-c", os.path.join(CSRC, src), "-o", obj])
-    probe_tmp = PROBE_LIB + f".tmp{os.getpid()}"
-    jobs.append([nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "static",
-                 os.path.join(CSRC, "probe_l2.cu"), "-o", probe_tmp])
     for src in CPP_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         jobs.append([nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-x", "c++",
@@ -79,7 +75,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
-    os.replace(probe_tmp, PROBE_LIB)
     return LIB
 
 

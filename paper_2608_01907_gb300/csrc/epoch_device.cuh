@@ -41,7 +41,7 @@ namespace {
 template <bool RED>
 __device__ __forceinline__ void apply_partner(float2 *pos, int32_t idx, float2 newv, float2 delta) {
     if (RED)
-        atomicAdd(pos + idx, delta);
+        add_pos(pos + idx, delta);
     else
         exchange_pos(pos + idx, newv);
 }
@@ -254,7 +254,7 @@ __device__ __forceinline__ void write_oriented_source(const OrientedArgs &a, int
     if (RED) {
         const float together = (float)pieces * a.inflight_share;
         const float inv = together > 1.0f ? 1.0f / together : 1.0f;
-        atomicAdd(a.pos + row, make_float2((yi.x - yi0.x) * inv, (yi.y - yi0.y) * inv));
+        add_pos(a.pos + row, make_float2((yi.x - yi0.x) * inv, (yi.y - yi0.y) * inv));
     } else {
         exchange_pos(a.pos + row, yi);
     }
@@ -281,16 +281,25 @@ __device__ __forceinline__ int row_pieces(int64_t row_begin, int64_t row_end, in
 
 // One chunk: the source y_i of the current row is held in registers and
 // written back when the walk leaves the row.
+// SNAP_ENT_PREFETCH (build switch): each entry of the chunk is loaded while
+// the previous one is processed (the first together with the slot
+// descriptor), so the stream's latency overlaps the gathers and updates.
+#ifndef SNAP_ENT_PREFETCH
+#define SNAP_ENT_PREFETCH 0
+#endif
 template <bool RED, int G, bool MULTI, bool W, bool E>
 __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t slot, uint32_t &flags, float &en) {
+    const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
+    const int64_t step = chunk_group_width(slot, a.num_segs);
+#if SNAP_ENT_PREFETCH
+    int4 ent_next = load_entry(ep);   // every stored chunk has at least one entry
+#endif
     const int2 mt = __ldg(a.meta + slot);   // {row of the first entry, chunk}
     int32_t row = mt.x;
     int64_t p = (int64_t)mt.y * a.seg_len;
     const int64_t p1 = p + a.seg_len < a.nnz ? p + a.seg_len : a.nnz;
     int64_t row_begin = RED ? __ldg(a.row_ptr + row) : 0;
     int64_t row_end = __ldg(a.row_ptr + row + 1);
-    const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
-    const int64_t step = chunk_group_width(slot, a.num_segs);
     GraphCtx c = graph_ctx<MULTI>(a, row);
     float2 yi = load_pos(a.pos + row);
     float2 yi0 = yi;
@@ -307,8 +316,14 @@ __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t sl
             yi = load_pos(a.pos + row);
             yi0 = yi;
         }
+#if SNAP_ENT_PREFETCH
+        const int4 ent = ent_next;   // {j, indices of (i, j) and (j, i): low bits, bits 32..47}
+        if (p + 1 < p1) ent_next = load_entry(ep + step);
+        if (!c.active) continue;
+#else
         if (!c.active) continue;
         const int4 ent = load_entry(ep);   // {j, indices of (i, j) and (j, i): low bits, bits 32..47}
+#endif
         const int64_t e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
         const int64_t e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
         oriented_entry<RED, G, W, E>(a, c, row, ent.x, e1, e2, yi, en);

@@ -3,8 +3,12 @@
 Jobs (a graph, initial positions, a seed) arrive at any time.  Each tick of
 the server:
   1. admits waiting jobs, first come first served, while a slot is free and
-     their estimated device memory fits the HBM budget (the graph is copied
-     to the device and prepared: snap_layout_create);
+     the job's peak device memory during preparation fits both the server's
+     HBM budget and the device's free memory as the driver reports it
+     (cudaMemGetInfo, read once per tick); the graph is copied to the device
+     and prepared (snap_layout_create), and the job's reservation is then
+     cut to what its handle really holds (snap_layout_device_bytes) plus its
+     positions;
   2. runs ONE multi-handle epoch launch (snap_multi_epoch) that advances every
      admitted job by one epoch, each at its own epoch index;
   3. retires jobs that ran all their epochs: their positions are copied back
@@ -26,13 +30,19 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (MODE_HOGWILD_RED, MultiEpoch, SnapSchedule, linear_schedule, make_options, snap_layout_create,
-               snap_layout_destroy)
+               snap_layout_destroy, snap_layout_device_bytes)
 
 
 def estimated_bytes(n: int, nnz: int) -> int:
-    """Peak device bytes of one job while it is prepared and while it runs:
-    CSR copy, orientation scan buffers and oriented entries, plus positions."""
+    """Peak device bytes of one job while it is prepared (an upper bound):
+    CSR copy, orientation scan buffers and the oriented entries in both
+    orders, plus positions.  Once prepared, a job holds less: its handle's
+    snap_layout_device_bytes plus its positions."""
     return 48 * nnz + 40 * (n + 1) + (1 << 20)
+
+
+# device memory left free for everything else on the GPU when admitting
+FREE_MARGIN = 256 << 20
 
 
 @dataclass
@@ -122,19 +132,23 @@ class LayoutServer:
     # -- one tick -----------------------------------------------------------
     def _admit(self) -> None:
         torch = self.torch
+        if not self.waiting or len(self.active) >= self.max_jobs:
+            return
+        free = torch.cuda.mem_get_info()[0] - FREE_MARGIN
         while self.waiting and len(self.active) < self.max_jobs:
             job = self.waiting[0]
             need = estimated_bytes(job.n, job.nnz)
-            if self.used + need > self.budget:
+            if self.used + need > self.budget or need > free:
                 break
             self.waiting.popleft()
-            self.used += need
-            job.reserved = need
             with torch.cuda.stream(self.prep):
                 job.handle = snap_layout_create(job.row_ptr, job.col_idx, None, job.n, self.opts, self.prep)
                 job.pos_dev = torch.from_numpy(job.positions).pin_memory().to("cuda", non_blocking=True)
             job.pos_dev.record_stream(self.stream)
             self.stream.wait_stream(self.prep)
+            job.reserved = snap_layout_device_bytes(job.handle) + job.positions.nbytes
+            self.used += job.reserved
+            free -= job.reserved
             job.admitted = self.clock()
             job.epoch = 0
             self.active.append(job)
