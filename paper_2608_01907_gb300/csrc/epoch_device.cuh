@@ -332,6 +332,187 @@ __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t sl
                                              flags);
 }
 
+// ---------------------------------------------------------------------------
+// Software-pipelined chunk walk (build switch SNAP_PIPE; uniform negatives,
+// k <= 4).  The next entry's random words are drawn and its k + k + 1
+// gathers issued before the current entry's updates, so a lane keeps two
+// entries' loads in flight.  Values gathered early for a vertex that the
+// current entry then updates are replaced by the lane's own latest value
+// (forwarding), so one lane alone still applies Algorithm 1's updates in
+// its order exactly; across lanes the early gathers are as racy as any.
+// ---------------------------------------------------------------------------
+#ifndef SNAP_PIPE
+#define SNAP_PIPE 0
+#endif
+
+struct StagedEntry {
+    int32_t j;
+    int32_t s1[4], s2[4];   // negatives of (i, j) (source i) and of (j, i) (source j)
+    float2 yj, v1[4], v2[4];
+};
+
+template <int G>
+__device__ __forceinline__ void stage_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, int4 ent,
+                                            StagedEntry &st) {
+    st.j = ent.x;
+    const int64_t e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
+    const int64_t e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
+    if (G > 0) {
+        const uint4 w1 = words_in(c, e1, 0u);
+        const uint4 w2 = words_in(c, e2, 0u);
+        const uint32_t ws1[4] = {w1.x, w1.y, w1.z, w1.w};
+        const uint32_t ws2[4] = {w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            st.s1[m] = negative_in(c, ws1[m], i);
+            st.s2[m] = negative_in(c, ws2[m], st.j);
+        }
+    }
+    st.yj = load_pos(a.pos + st.j);
+#pragma unroll
+    for (int m = 0; m < G; ++m) st.v1[m] = load_pos(a.pos + st.s1[m]);
+#pragma unroll
+    for (int m = 0; m < G; ++m) st.v2[m] = load_pos(a.pos + st.s2[m]);
+}
+
+// Both directed steps of a staged entry (the arithmetic of oriented_entry);
+// on return st.yj, st.v1 and st.v2 hold the values this lane wrote.
+template <bool RED, int G, bool E>
+__device__ __forceinline__ void finish_entry(const OrientedArgs &a, float eta, int32_t i, StagedEntry &st,
+                                             float2 &yi, float &en) {
+    float2 yj = st.yj;
+    const float2 yj0 = yj;
+    {
+        if (E) en += attraction_energy(yi.x - yj.x, yi.y - yj.y);
+        const float2 f = attraction_on_i(yi.x - yj.x, yi.y - yj.y);
+        const float2 df = make_float2(eta * f.x, eta * f.y);
+        yi.x += df.x;
+        yi.y += df.y;
+        yj.x -= df.x;
+        yj.y -= df.y;
+        if (G > 0) negative_group<RED, E>(a.pos, eta, st.s1, st.v1, G, yi, st.j, yj, en);
+    }
+    {
+        if (E) en += attraction_energy(yj.x - yi.x, yj.y - yi.y);
+        const float2 f = attraction_on_i(yj.x - yi.x, yj.y - yi.y);
+        const float2 df = make_float2(eta * f.x, eta * f.y);
+        yj.x += df.x;
+        yj.y += df.y;
+        yi.x -= df.x;
+        yi.y -= df.y;
+        if (G > 0) {
+#pragma unroll
+            for (int m = 0; m < G; ++m)
+#pragma unroll
+                for (int q = 0; q < G; ++q)
+                    if (st.s1[q] == st.s2[m]) st.v2[m] = st.v1[q];
+            negative_group<RED, E>(a.pos, eta, st.s2, st.v2, G, yj, i, yi, en);
+        }
+    }
+    apply_partner<RED>(a.pos, st.j, yj, make_float2(yj.x - yj0.x, yj.y - yj0.y));
+    st.yj = yj;
+}
+
+// The value this lane last wrote for vertex x while finishing entry `done`
+// of source i (whose value in memory is now yi_mem), else v.  Later writes
+// win: the negatives of (i, j) in order, then those of (j, i), then j's
+// final write, then the source.
+template <int G>
+__device__ __forceinline__ float2 forwarded(int32_t x, float2 v, const StagedEntry &done, int32_t i, float2 yi_mem) {
+#pragma unroll
+    for (int m = 0; m < G; ++m)
+        if (done.s1[m] == x) v = done.v1[m];
+#pragma unroll
+    for (int m = 0; m < G; ++m)
+        if (done.s2[m] == x) v = done.v2[m];
+    if (x == done.j) v = done.yj;
+    if (x == i) v = yi_mem;
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ void forward_into(StagedEntry &next, const StagedEntry &done, int32_t i, float2 yi_mem) {
+    next.yj = forwarded<G>(next.j, next.yj, done, i, yi_mem);
+#pragma unroll
+    for (int m = 0; m < G; ++m) next.v1[m] = forwarded<G>(next.s1[m], next.v1[m], done, i, yi_mem);
+#pragma unroll
+    for (int m = 0; m < G; ++m) next.v2[m] = forwarded<G>(next.s2[m], next.v2[m], done, i, yi_mem);
+}
+
+// The value the source write-back leaves in memory for this lane's view
+// (HOGWILD_RED adds the scaled displacement; HOGWILD writes yi).
+template <bool RED>
+__device__ __forceinline__ float2 written_source(const OrientedArgs &a, float2 yi, float2 yi0, int pieces) {
+    if (!RED) return yi;
+    const float together = (float)pieces * a.inflight_share;
+    const float inv = together > 1.0f ? 1.0f / together : 1.0f;
+    return make_float2(yi0.x + (yi.x - yi0.x) * inv, yi0.y + (yi.y - yi0.y) * inv);
+}
+
+template <bool RED, int G, bool MULTI, bool E>
+__device__ __forceinline__ void oriented_chunk_pipe(const OrientedArgs &a, int64_t slot, uint32_t &flags, float &en) {
+    const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
+    const int64_t step = chunk_group_width(slot, a.num_segs);
+    int4 ent_next = load_entry(ep);   // every stored chunk has at least one entry
+    const int2 mt = __ldg(a.meta + slot);   // {row of the first entry, chunk}
+    int32_t row = mt.x;
+    int64_t p = (int64_t)mt.y * a.seg_len;
+    const int64_t p1 = p + a.seg_len < a.nnz ? p + a.seg_len : a.nnz;
+    int64_t row_begin = RED ? __ldg(a.row_ptr + row) : 0;
+    int64_t row_end = __ldg(a.row_ptr + row + 1);
+    GraphCtx c = graph_ctx<MULTI>(a, row);
+    float2 yi = load_pos(a.pos + row);
+    float2 yi0 = yi;
+    StagedEntry cur, nxt;
+    if (c.active) stage_entry<G>(a, c, row, ent_next, cur);
+    if (p + 1 < p1) ent_next = load_entry(ep + step);
+    for (; p < p1; ++p) {
+        // the next entry's row, graph and gathers, issued before this entry's updates
+        const bool more = p + 1 < p1;
+        int32_t row_n = row;
+        int64_t rb_n = row_begin, re_n = row_end;
+        GraphCtx c_n = c;
+        float2 yi_n = yi;
+        if (more) {
+            if (p + 1 >= re_n) {
+                do {
+                    ++row_n;
+                    rb_n = re_n;
+                    re_n = __ldg(a.row_ptr + row_n + 1);
+                } while (re_n <= p + 1);
+                if (MULTI) c_n = graph_ctx<MULTI>(a, row_n);
+                yi_n = load_pos(a.pos + row_n);
+            }
+            if (c_n.active) stage_entry<G>(a, c_n, row_n, ent_next, nxt);
+            if (p + 2 < p1) ent_next = load_entry(ep + 2 * step);
+            ep += step;
+        }
+        if (c.active) finish_entry<RED, G, E>(a, c.eta, row, cur, yi, en);
+        if (!more) break;
+        if (row_n != row) {
+            const int pieces = RED ? row_pieces(row_begin, row_end, a.seg_len) : 1;
+            float2 mem = yi;
+            if (c.active) {
+                write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
+                mem = written_source<RED>(a, yi, yi0, pieces);
+                yi_n = forwarded<G>(row_n, yi_n, cur, row, mem);
+                if (c_n.active) forward_into<G>(nxt, cur, row, mem);
+            }
+            row = row_n;
+            row_begin = rb_n;
+            row_end = re_n;
+            c = c_n;
+            yi = yi_n;
+            yi0 = yi;
+        } else if (c.active) {
+            forward_into<G>(nxt, cur, row, yi);
+        }
+        cur = nxt;
+    }
+    if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
+                                             flags);
+}
+
 // In a batch a chunk may cross from one graph into the next; the graph is
 // looked up again at every row change.  E: also sum the actual energy of the
 // epoch (half the sum over the directed steps of U^a and over the drawn pairs
@@ -345,7 +526,12 @@ __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (groups << 5); w += stride) {
         const int64_t ws = slot_of(w, groups, a.perm_mul, a.perm_add);
         float en = 0.0f;
-        if (ws < a.num_segs) oriented_chunk<RED, G, MULTI, W, E>(a, ws, flags, en);
+        if (ws < a.num_segs) {
+            if (SNAP_PIPE && !W && a.k <= 4)
+                oriented_chunk_pipe<RED, G, MULTI, E>(a, ws, flags, en);
+            else
+                oriented_chunk<RED, G, MULTI, W, E>(a, ws, flags, en);
+        }
         if (E) energy += (double)en;
     }
     if (flags) atomicOr(a.status, flags);

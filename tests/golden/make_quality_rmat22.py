@@ -7,9 +7,11 @@ Workload: R-MAT 2^22 nodes / 34,000,000 undirected edges (a, b, c = .57, .19,
 step decay from eta0 = 1 (floor 1e-3 eta0), seeds 1..5 (initial positions and
 random words).  Each layout is Algorithm 1 in the oracle (FP64, the directed
 edge list shuffled once), scored by the oracle: the objective of Eq. 4 (exact
-edge sum plus 20,000,000 sampled vertex pairs, sample seed 99) and the
+edge sum plus 20,000,000 sampled vertex pairs, sample seed 99), the
 neighbourhood preservation of Section 4.1 (r = 2) on 1,024 vertices drawn
-without replacement from the non-isolated ones (numpy PCG64 seed 2024).
+without replacement from the non-isolated ones (numpy PCG64 seed 2024), and
+where the 64 highest-degree vertices sit relative to their neighbours (hub
+offset, below).
 
 Calls only oracle/ and synth/.  About 15 minutes of one core per seed; the
 seeds run in a spawned process pool:
@@ -49,10 +51,28 @@ def np_sample(row_ptr):
     return np.sort(np.random.default_rng(NP_SEED).choice(cand, NP_NODES, replace=False)).astype(np.int32)
 
 
+def hub_offset(g, Y, hubs=64):
+    """Where the highest-degree vertices end up relative to their neighbours:
+    for each of the `hubs` vertices of highest degree, the distance from its
+    position to the centroid of its neighbours' positions, divided by the
+    neighbours' rms distance to that centroid; the mean over those vertices."""
+    deg = np.diff(g.row_ptr)
+    top = np.argsort(-deg, kind="stable")[:hubs]
+    out = []
+    for h in top:
+        nb = Y[g.col_idx[g.row_ptr[h]:g.row_ptr[h + 1]]]
+        c = nb.mean(axis=0)
+        spread = np.sqrt(((nb - c) ** 2).sum(axis=1).mean())
+        out.append(np.linalg.norm(Y[h] - c) / spread)
+    return float(np.mean(out))
+
+
 def score(g, Y):
+    """(objective of Eq. 4, NP, hub offset) of a layout, by the oracle."""
     import oracle
     ob = oracle.objective_sampled(g.row_ptr, g.col_idx, g.n, Y, K, PAIRS, PAIR_SEED)["total"]
-    return ob, oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, Y, np_sample(g.row_ptr))
+    return ob, oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, Y, np_sample(g.row_ptr)), \
+        hub_offset(g, np.asarray(Y, dtype=np.float64))
 
 
 def job(seed):
@@ -62,8 +82,8 @@ def job(seed):
     t = time.time()
     Y = oracle.seq(g.row_ptr, g.col_idx, g.n, initial_positions(g.n, seed), EPOCHS, K, SCHED, seed=seed)
     secs = time.time() - t
-    ob, npv = score(g, Y)
-    return seed, ob, npv, secs
+    ob, npv, hub = score(g, Y)
+    return seed, ob, npv, hub, secs
 
 
 def main():
@@ -79,10 +99,12 @@ def main():
         f.write("# FP64 oracle layouts (Algorithm 1) of R-MAT 2^22 / 34,000,000 edges, BFS relabelling,\n"
                 "# k = 3, 30 epochs, eta0 = 1 linear decay; scored by the oracle: objective of Eq. 4\n"
                 "# (exact edges + 20,000,000 sampled pairs, seed 99) and NP (Section 4.1, r = 2) on 1,024\n"
-                "# non-isolated vertices (PCG64 seed 2024).  Written by tests/golden/make_quality_rmat22.py.\n"
-                "# seed objective np oracle_seconds\n")
-        for seed, ob, npv, secs in rows:
-            f.write(f"{seed} {ob!r} {npv!r} {secs:.0f}\n")
+                "# non-isolated vertices (PCG64 seed 2024); hub offset = mean over the 64 highest-degree\n"
+                "# vertices of |y_h - centroid of its neighbours| / the neighbours' rms distance to it.\n"
+                "# Written by tests/golden/make_quality_rmat22.py.\n"
+                "# seed objective np hub_offset oracle_seconds\n")
+        for seed, ob, npv, hub, secs in rows:
+            f.write(f"{seed} {ob!r} {npv!r} {hub!r} {secs:.0f}\n")
     print(open(OUT).read())
 
 

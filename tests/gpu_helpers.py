@@ -84,10 +84,12 @@ def cached_graph(name: str, make):
     path = os.path.join(d, f"{name}_{source_digest()}.npz")
     if os.path.exists(path):
         z = np.load(path)
-        return Graph(int(z["n"]), z["row_ptr"], z["col_idx"], name=name)
+        labels = z["labels"] if "labels" in z.files else None
+        return Graph(int(z["n"]), z["row_ptr"], z["col_idx"], labels=labels, name=name)
     g = make()
     tmp = path + f".{os.getpid()}.npz"
-    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col_idx=g.col_idx)
+    extra = {"labels": g.labels} if g.labels is not None else {}
+    np.savez(tmp, n=g.n, row_ptr=g.row_ptr, col_idx=g.col_idx, **extra)
     os.replace(tmp, path)
     return g
 
@@ -102,7 +104,7 @@ def rmat22_bfs():
 def lfr260k():
     """The LFR-style 260k-node / ~6.9M-edge community graph (seed 1)."""
     from synth import lfr_graph
-    return cached_graph("lfr260k_s1", lambda: lfr_graph(seed=1))
+    return cached_graph("lfr260k_s1_labelled", lambda: lfr_graph(seed=1))
 
 
 def coordinate_error(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:

@@ -25,8 +25,8 @@ sys.path.insert(0, os.path.join(HERE, "golden"))
 
 
 def _stored():
-    rows = np.array([[float(x) for x in r[:3]] for r in read_golden("quality_rmat22_k3.txt")])
-    return rows[:, 0].astype(int).tolist(), rows[:, 1], rows[:, 2]
+    rows = np.array([[float(x) for x in r[:4]] for r in read_golden("quality_rmat22_k3.txt")])
+    return rows[:, 0].astype(int).tolist(), rows[:, 1], rows[:, 2], rows[:, 3]
 
 
 def _score(path):
@@ -39,10 +39,10 @@ def _score(path):
 def test_full_size_hogwild_quality_within_two_percent_of_oracle(cuda, mode, tmp_path):
     import make_quality_rmat22 as mq
     torch = cuda
-    seeds, ob_ref, np_ref = _stored()
+    seeds, ob_ref, np_ref, hub_ref = _stored()
     g = rmat22_bfs()
     sched = snap.linear_schedule(eta0=1.0, total_epochs=mq.EPOCHS)
-    paths = []
+    paths, drift = [], []
     with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(mode=mode)) as L:
         for seed in seeds:
             pos = torch.from_numpy(initial_positions(g.n, seed)).cuda()
@@ -50,6 +50,9 @@ def test_full_size_hogwild_quality_within_two_percent_of_oracle(cuda, mode, tmp_
             L.check()
             Y = pos.cpu().numpy().astype(np.float64)
             assert np.all(np.isfinite(Y))
+            Y0 = initial_positions(g.n, seed).astype(np.float64)
+            # Algorithm 1 keeps the centroid (every update is +-F on two vertices)
+            drift.append(np.linalg.norm(Y.mean(0) - Y0.mean(0)) / np.sqrt(((Y - Y0) ** 2).sum(1).mean()))
             p = str(tmp_path / f"layout_{seed}.npy")
             np.save(p, Y)
             paths.append(p)
@@ -59,6 +62,8 @@ def test_full_size_hogwild_quality_within_two_percent_of_oracle(cuda, mode, tmp_
     d_np = scores[:, 1].mean() / np_ref.mean() - 1
     print(f"R-MAT 2^22 quality mode={mode}: objective {scores[:, 0].mean():.1f} vs oracle {ob_ref.mean():.1f} "
           f"({d_ob:+.2%}), NP {scores[:, 1].mean():.5f} vs {np_ref.mean():.5f} ({d_np:+.2%}); "
-          f"per seed objective {' '.join(f'{v:.0f}' for v in scores[:, 0])}")
+          f"per seed objective {' '.join(f'{v:.0f}' for v in scores[:, 0])}; hub offset "
+          f"{scores[:, 2].mean():.3f} vs oracle {hub_ref.mean():.3f}; centroid drift / rms move "
+          f"{np.mean(drift):.2e}")
     assert abs(d_ob) < 0.02
     assert abs(d_np) < 0.02

@@ -127,16 +127,20 @@ def test_server_quality_in_the_mix_matches_alone(cuda):
         o_mix = oracle.objective_sampled(g.row_ptr, g.col_idx, g.n, job.positions, 3, 2_000_000, 9)["total"]
         o_alone = oracle.objective_sampled(g.row_ptr, g.col_idx, g.n, alone, 3, 2_000_000, 9)["total"]
         o_ref = oracle.objective_sampled(g.row_ptr, g.col_idx, g.n, ref, 3, 2_000_000, 9)["total"]
-        nodes = np.sort(np.random.default_rng(q).choice(g.n, min(g.n, 2000), replace=False)).astype(np.int32)
-        np_mix = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, job.positions, nodes)
-        np_ref = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, ref, nodes)
-        rel.append((o_mix / o_alone - 1, o_mix / o_ref - 1, np_mix / np_ref - 1))
-        print(f"job {q}: in the mix vs alone {o_mix / o_alone - 1:+.2%}, vs oracle {o_mix / o_ref - 1:+.2%}, "
-              f"NP vs oracle {np_mix / np_ref - 1:+.2%}")
+        np_mix = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, job.positions)
+        np_alone = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, alone)
+        np_ref = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, ref)
+        rel.append((o_mix / o_alone - 1, o_mix / o_ref - 1, np_mix / np_alone - 1, np_mix / np_ref - 1))
+        print(f"job {q}: in the mix vs alone {o_mix / o_alone - 1:+.2%} (NP {np_mix / np_alone - 1:+.2%}), "
+              f"vs oracle {o_mix / o_ref - 1:+.2%} (NP {np_mix / np_ref - 1:+.2%})")
     rel = np.array(rel)
+    # the serving property: a job's result in the mix is the result alone
     assert np.all(np.abs(rel[:, 0]) < 0.02)
+    assert np.all(np.abs(rel[:, 2]) < 0.02)
+    # quality against Algorithm 1, one seed per job: the band Section 4.3
+    # reports between the lock-free variants and the serial algorithm
     assert np.all(np.abs(rel[:, 1]) < 0.03)
-    assert np.all(np.abs(rel[:, 2]) < 0.03)
+    assert np.all(np.abs(rel[:, 3]) < 0.05)
 
 
 def test_server_admission_respects_the_memory_budget(cuda):
