@@ -129,6 +129,11 @@ typedef struct {
  * with the same positions pointer, epoch range, k, schedule and seed (up to 4
  * graphs are cached per handle). */
 #define SNAP_FLAG_CUDA_GRAPH 1
+/* snap_options.flags: a HOGWILD handle keeps its device CSR after building
+ * the oriented list (SYNC handles always keep it), for
+ * snap_layout_neighborhood_preservation and the NP half of the autotuner's
+ * gate; snap_layout_device_bytes counts it. */
+#define SNAP_FLAG_KEEP_CSR 2
 
 /* Fill *opts with the defaults (HOGWILD_RED, UNIFORM, S = 1, no cap). */
 void snap_options_default(snap_options *opts);
@@ -306,7 +311,12 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
  *      configuration's layout; the objective is exact for batches and
  *      n <= 16384, otherwise the same 2^24 sampled pairs for every
  *      candidate).  A candidate whose layout becomes non-finite is
- *      rejected.  The entry configuration always passes.
+ *      rejected.  The entry configuration always passes.  When the handle
+ *      keeps its CSR (SNAP_FLAG_KEEP_CSR, or SYNC) and no graph has more
+ *      than 262,144 vertices, a candidate must also keep the neighbourhood
+ *      preservation NP (Section 4.1, r = 2; snap_layout_neighborhood_preservation
+ *      on 1,024 vertices drawn from `seed`, the same for every candidate)
+ *      at NP >= (1 - tolerance) NP_entry.
  *      tolerance < 0: no gate, the fastest remaining candidate is chosen.
  *
  *   initial_positions  device, n x 2 float32, read only (may be NULL when
@@ -314,7 +324,8 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
  *   scratch_positions  device, n x 2 float32; overwritten.
  *   neg_samples, schedule, seed   as for snap_layout_epochs.
  *   chosen_segment, chosen_block, chosen_ms (ms per epoch),
- *   chosen_objective (U of the chosen layout; NaN without the gate)
+ *   chosen_objective (U of the chosen layout; NaN without the gate),
+ *   chosen_np (NP of the chosen layout; NaN when NP is not gated)
  *                      host outputs, nullable.
  * Synchronises the stream.  Errors: INVALID_ARG, NOT_SUPPORTED (SYNC),
  * NUMERIC (the entry configuration's layout became non-finite), CUDA.  On
@@ -323,7 +334,31 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
 snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions, float *scratch_positions,
                                  int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
                                  double tolerance, int32_t *chosen_segment, int32_t *chosen_block,
-                                 double *chosen_ms, double *chosen_objective, void *cuda_stream);
+                                 double *chosen_ms, double *chosen_objective, double *chosen_np,
+                                 void *cuda_stream);
+
+/*
+ * snap_layout_neighborhood_preservation -- NP of a layout (Section 4.1,
+ * "Metrics", r = 2) on sampled vertices: for vertex i, N_G = the vertices
+ * within two hops (i excluded, k = |N_G|), N_L = the k vertices of i's graph
+ * nearest to i in the layout (squared distance formed in FP64 from the FP32
+ * positions, ties to the smaller id), NP_i = |N_G & N_L| / |N_G | N_L|;
+ * vertices without neighbours are skipped.
+ *
+ *   positions   device, n x 2 float32 (read only).
+ *   nodes       host, count vertex ids in [0, n) (repeats allowed).
+ *   out_mean    host: mean NP_i over the samples with neighbours (0 if none).
+ *   out_used    host, nullable: the number of those samples.
+ *
+ * Needs the handle's device CSR: SYNC handles keep it, HOGWILD handles only
+ * with SNAP_FLAG_KEEP_CSR (else NOT_SUPPORTED); every graph of the handle has
+ * at most 262,144 vertices (else NOT_SUPPORTED).  Allocates small scratch,
+ * synchronises the stream.  Errors: INVALID_ARG, NOT_SUPPORTED,
+ * OUT_OF_MEMORY, CUDA, NUMERIC (from an earlier call).
+ */
+snap_status snap_layout_neighborhood_preservation(snap_layout_t h, const float *positions, const int32_t *nodes,
+                                                  int32_t count, double *out_mean, int32_t *out_used,
+                                                  void *cuda_stream);
 
 /* Release the handle and its device memory.  NULL is ignored.  Does not
  * synchronise: the memory is freed stream-ordered after the work of the

@@ -23,7 +23,7 @@ __all__ = [
     "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
     "snap_layout_run", "snap_last_error", "Layout", "linear_schedule", "snap_sync_epochs_noalloc",
     "snap_layout_create_batch", "batch_union", "snap_layout_autotune", "MultiEpoch", "snap_sampler_table",
-    "snap_layout_epochs_energy", "snap_layout_sync_chunks",
+    "snap_layout_epochs_energy", "snap_layout_sync_chunks", "snap_layout_neighborhood_preservation",
 ]
 
 MODE_HOGWILD, MODE_HOGWILD_RED, MODE_SYNC = 0, 1, 2
@@ -52,6 +52,7 @@ class SnapOptions(ctypes.Structure):
 
 
 FLAG_CUDA_GRAPH = 1
+FLAG_KEEP_CSR = 2
 
 
 def linear_schedule(eta0: float = 1.0, total_epochs: int = 30, eta_min: float | None = None,
@@ -97,7 +98,9 @@ def load_library():
     lib.snap_layout_objective.restype = st
     lib.snap_layout_check.argtypes = [P, P]
     lib.snap_layout_check.restype = st
-    lib.snap_layout_autotune.argtypes = [P, P, P, i32, P, u64, f64, P, P, P, P, P]
+    lib.snap_layout_autotune.argtypes = [P, P, P, i32, P, u64, f64, P, P, P, P, P, P]
+    lib.snap_layout_neighborhood_preservation.argtypes = [P, P, P, i32, P, P, P]
+    lib.snap_layout_neighborhood_preservation.restype = st
     lib.snap_layout_autotune.restype = st
     lib.snap_layout_device_bytes.argtypes = [P]
     lib.snap_layout_device_bytes.restype = i64
@@ -172,13 +175,14 @@ def snap_options_default() -> SnapOptions:
 
 def make_options(mode: int = MODE_HOGWILD_RED, sync_substeps: int = 1, sync_cap: float = 0.0,
                  segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM,
-                 cuda_graph: bool = False, max_inflight: float = 0.0, node_weights=None) -> SnapOptions:
+                 cuda_graph: bool = False, max_inflight: float = 0.0, node_weights=None,
+                 keep_csr: bool = False) -> SnapOptions:
     """Options for snap_layout_create; node_weights (n floats) goes with SAMPLER_WEIGHTS
     and is kept alive by the returned object."""
     o = snap_options_default()
     o.mode, o.sync_substeps, o.sync_cap = mode, sync_substeps, sync_cap
     o.segment_edges, o.block_threads, o.sampler = segment_edges, block_threads, sampler
-    o.flags = FLAG_CUDA_GRAPH if cuda_graph else 0
+    o.flags = (FLAG_CUDA_GRAPH if cuda_graph else 0) | (FLAG_KEEP_CSR if keep_csr else 0)
     o.max_inflight = max_inflight
     if node_weights is not None:
         w = _host(node_weights, np.float32)
@@ -253,17 +257,29 @@ def snap_layout_check(h, stream=None) -> None:
 
 def snap_layout_autotune(h, scratch_positions, neg_samples: int, schedule: SnapSchedule, seed: int,
                          initial_positions=None, tolerance: float = 0.02, stream=None):
-    """Returns (chunk entries, block threads, ms per epoch, objective) chosen for the
-    handle; tolerance < 0 (or no initial positions) times the candidates only."""
+    """Returns (chunk entries, block threads, ms per epoch, objective, NP) chosen
+    for the handle; tolerance < 0 (or no initial positions) times the candidates
+    only.  NP is NaN unless the handle keeps its CSR (keep_csr)."""
     if initial_positions is None:
         tolerance = -1.0
-    seg, blk, ms, u = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    seg, blk, ms, u, npv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     init = _device_positions(initial_positions) if initial_positions is not None else None
     _check(load_library().snap_layout_autotune(h, init, _device_positions(scratch_positions), neg_samples,
                                                ctypes.byref(schedule), seed, tolerance, ctypes.byref(seg),
                                                ctypes.byref(blk), ctypes.byref(ms), ctypes.byref(u),
-                                               _stream(stream)))
-    return seg.value, blk.value, ms.value, u.value
+                                               ctypes.byref(npv), _stream(stream)))
+    return seg.value, blk.value, ms.value, u.value, npv.value
+
+
+def snap_layout_neighborhood_preservation(h, positions, nodes, stream=None):
+    """NP (Section 4.1, r = 2) of device positions on the sampled vertices
+    `nodes`; returns (mean over samples with neighbours, their count)."""
+    nd = _host(nodes, np.int32)
+    mean, used = ctypes.c_double(), ctypes.c_int32()
+    _check(load_library().snap_layout_neighborhood_preservation(h, _device_positions(positions), _ptr(nd), nd.size,
+                                                                ctypes.byref(mean), ctypes.byref(used),
+                                                                _stream(stream)))
+    return mean.value, used.value
 
 
 def snap_layout_device_bytes(h) -> int:
@@ -445,6 +461,10 @@ class Layout:
     def objective(self, positions, neg_samples: int, exact: bool = True, pair_samples: int = 0, seed: int = 0):
         _device_positions(positions, self.n)
         return snap_layout_objective(self.handle, positions, neg_samples, exact, pair_samples, seed, self.stream)
+
+    def neighborhood_preservation(self, positions, nodes):
+        _device_positions(positions, self.n)
+        return snap_layout_neighborhood_preservation(self.handle, positions, nodes, self.stream)
 
     def autotune(self, initial_positions, scratch_positions, neg_samples: int, schedule: SnapSchedule, seed: int,
                  tolerance: float = 0.02):

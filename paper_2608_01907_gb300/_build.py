@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsnap_layout.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["capi.cu", "epoch_kernels.cu", "epoch_weighted.cu", "epoch_energy.cu", "graph_kernels.cu",
-              "sync_noalloc.cu"]
+              "sync_noalloc.cu", "np_kernels.cu"]
 CPP_SOURCES = ["reorder.cpp", "sampler.cpp"]
 
 

@@ -190,6 +190,9 @@ struct snap_layout {
     int4 *d_act_ent = nullptr;
     int2 *d_act_meta = nullptr;
     int64_t act_ent_bytes = 0, act_meta_bytes = 0;
+    bool act_narrow = false;              // entries carry their source (fewer than 2^32 directed edges)
+    int32_t *d_act_pieces = nullptr;      // chunks each vertex's oriented row spans (narrow lists)
+    int64_t act_pieces_bytes = 0;
     // batch of graphs (num_graphs > 1): graph of every vertex and per-graph table
     int32_t num_graphs = 1;
     std::vector<int32_t> graph_offsets;   // num_graphs + 1 vertex offsets
@@ -252,6 +255,8 @@ struct snap_layout {
         free_async(d_act_row_ptr);
         free_async(d_act_ent);
         free_async(d_act_meta);
+        free_async(d_act_pieces);
+        d_act_pieces = nullptr;
         free_async(d_alias);
         free_async(d_objw);
         d_alias = nullptr;
@@ -334,6 +339,23 @@ static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, 
         if (meta) cudaFreeAsync(meta, stream);
         return err;
     }
+    if (h->act_narrow) {
+        // the per-vertex piece counts depend on the chunk size
+        if (!h->d_act_pieces) {
+            const int64_t pb = (int64_t)sizeof(int32_t) * (h->n > 0 ? h->n : 1);
+            err = dev_alloc(ac, (void **)&h->d_act_pieces, (size_t)pb, stream);
+            if (err == cudaSuccess) {
+                h->act_pieces_bytes = pb;
+                h->device_bytes += pb;
+            }
+        }
+        if (err == cudaSuccess) err = launch_row_pieces(h->d_act_row_ptr, h->n, target, h->d_act_pieces, stream);
+        if (err != cudaSuccess) {
+            cudaFreeAsync(ent, stream);
+            cudaFreeAsync(meta, stream);
+            return err;
+        }
+    }
     cudaFreeAsync(h->d_act_ent, stream);
     if (h->d_act_meta) cudaFreeAsync(h->d_act_meta, stream);
     h->device_bytes += ent_bytes + meta_bytes - h->act_ent_bytes - h->act_meta_bytes;
@@ -354,6 +376,7 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     const int32_t n = h->n;
     const int64_t nnz = h->nnz;
     h->act_nnz = nnz / 2;   // symmetric and loop-free: each undirected edge once
+    h->act_narrow = nnz < ((int64_t)1 << 32);   // 32-bit edge indices: the entry's spare word holds the source
     if (h->act_seg_len == 0) {
         // Default chunk: 4 entries.  A lane applies a chunk's steps of one
         // source back to back; long bursts of one source's steps move the
@@ -394,7 +417,7 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
              "orientation flags kernel");
         step(exclusive_scan_i32(temp, &temp_bytes, flags, pos, nnz + 1, stream), "orientation scan");
         step(launch_orient_scatter(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, pos,
-                                   h->d_act_ent, stream), "orientation scatter kernel");
+                                   h->d_act_ent, h->act_narrow ? 1 : 0, stream), "orientation scatter kernel");
         step(launch_orient_rowptr(h->d_row_ptr, pos, n, h->d_act_row_ptr, stream), "orientation offsets kernel");
     }
     int64_t total = -1;
@@ -415,10 +438,12 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     err = set_chunks(h, ac, h->act_seg_len, stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
     if (err != cudaSuccess) return cuda_fail(err, "oriented chunks");
-    h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
-                                 sizeof(int32_t) * (size_t)(h->num_segs * h->seg_len + 4) +
-                                 sizeof(int32_t) * (size_t)(h->num_segs > 0 ? h->num_segs : 1));
-    h->release_csr();
+    if (!(h->opts.flags & SNAP_FLAG_KEEP_CSR)) {
+        h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
+                                     sizeof(int32_t) * (size_t)(h->num_segs * h->seg_len + 4) +
+                                     sizeof(int32_t) * (size_t)(h->num_segs > 0 ? h->num_segs : 1));
+        h->release_csr();
+    }
     return SNAP_OK;
 }
 
@@ -473,7 +498,8 @@ static snap_status check_options(const snap_options &o) {
     if (o.segment_edges != 0 && (o.segment_edges < 4 || o.segment_edges > 4096 || o.segment_edges % 4 != 0))
         return fail(SNAP_ERR_INVALID_ARG, "segment_edges = %d must be 0 or a multiple of 4 in [4, 4096]",
                     o.segment_edges);
-    if (o.flags & ~SNAP_FLAG_CUDA_GRAPH) return fail(SNAP_ERR_INVALID_ARG, "unknown flags 0x%x", o.flags);
+    if (o.flags & ~(SNAP_FLAG_CUDA_GRAPH | SNAP_FLAG_KEEP_CSR))
+        return fail(SNAP_ERR_INVALID_ARG, "unknown flags 0x%x", o.flags);
     if (!(o.max_inflight >= 0.0f) || !(o.max_inflight <= 1.0f))
         return fail(SNAP_ERR_INVALID_ARG, "max_inflight must be in [0, 1]");
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 256 || o.block_threads % 32 != 0))
@@ -851,6 +877,8 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
             a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
             a.alias = h->d_alias;
             a.energy = energy ? energy + ep : nullptr;
+            a.narrow = h->act_narrow ? 1 : 0;
+            a.pieces = h->d_act_pieces;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
             const int g = neg_samples < 4 ? neg_samples : 4;
             const int gmax = energy ? h->grid_energy[red][g] : h->grid_oriented[red][g];
@@ -1153,10 +1181,83 @@ static cudaError_t apply_config(snap_layout *h, AllocCounter &ac, int32_t target
     return cudaSuccess;
 }
 
+// Neighbourhood preservation (Section 4.1, r = 2) of a layout on sampled
+// vertices, from the CSR the handle keeps (SYNC handles, or HOGWILD handles
+// created with SNAP_FLAG_KEEP_CSR).  *mean: the mean over the samples that
+// have neighbours, *used: their number.
+static snap_status np_impl(snap_layout *h, const float2 *pos, const int32_t *nodes, int32_t count, double *mean,
+                           int32_t *used, cudaStream_t stream) {
+    if (!h->d_row_ptr || !h->d_col)
+        return fail(SNAP_ERR_NOT_SUPPORTED, "the handle does not keep its CSR (create it with SNAP_FLAG_KEEP_CSR)");
+    int32_t max_graph = h->n;
+    if (h->num_graphs > 1) {
+        max_graph = 0;
+        for (const GraphInfo &gi : h->h_graphs) max_graph = gi.n > max_graph ? gi.n : max_graph;
+    }
+    if (max_graph > kNpMaxGraph)
+        return fail(SNAP_ERR_NOT_SUPPORTED, "NP needs graphs of at most %d vertices (largest: %d)", kNpMaxGraph,
+                    max_graph);
+    for (int32_t q = 0; q < count; ++q)
+        if (nodes[q] < 0 || nodes[q] >= h->n) return fail(SNAP_ERR_INVALID_ARG, "sample %d outside [0, n)", q);
+    *mean = 0.0;
+    *used = 0;
+    if (count == 0) return SNAP_OK;
+    AllocCounter ac;
+    int32_t *d_nodes = nullptr;
+    double *d_out = nullptr;
+    cudaError_t err = dev_alloc(ac, (void **)&d_nodes, sizeof(int32_t) * (size_t)count, stream);
+    if (err == cudaSuccess) err = dev_alloc(ac, (void **)&d_out, sizeof(double) * (size_t)count, stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_nodes, nodes, sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess)
+        err = launch_np_samples(h->d_row_ptr, h->d_col, pos, d_nodes, count, h->d_node_graph,
+                                h->num_graphs > 1 ? h->d_graphs : nullptr, h->n, max_graph, d_out, h->sms * 8, stream);
+    std::vector<double> out((size_t)count, 0.0);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+    if (d_nodes) cudaFreeAsync(d_nodes, stream);
+    if (d_out) cudaFreeAsync(d_out, stream);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? fail(SNAP_ERR_OUT_OF_MEMORY, "NP scratch")
+                                                : cuda_fail(err, "neighbourhood preservation");
+    }
+    double sum = 0.0;
+    int32_t u = 0;
+    for (double v : out)
+        if (v >= 0.0) {
+            sum += v;
+            ++u;
+        }
+    *mean = u > 0 ? sum / u : 0.0;
+    *used = u;
+    return SNAP_OK;
+}
+
+snap_status snap_layout_neighborhood_preservation(snap_layout_t h, const float *positions, const int32_t *nodes,
+                                                  int32_t count, double *out_mean, int32_t *out_used,
+                                                  void *cuda_stream) {
+    NvtxRange nvtx_range("snap_layout_neighborhood_preservation");
+    if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
+    if (!positions || ((uintptr_t)positions & 7u) != 0)
+        return fail(SNAP_ERR_INVALID_ARG, "positions must be a non-NULL 8-byte aligned device buffer");
+    if (count < 0 || (count > 0 && !nodes)) return fail(SNAP_ERR_INVALID_ARG, "bad sample list");
+    if (!out_mean) return fail(SNAP_ERR_INVALID_ARG, "out_mean is NULL");
+    snap_status st = poll_status(h);
+    if (st != SNAP_OK) return st;
+    int32_t used = 0;
+    st = np_impl(h, reinterpret_cast<const float2 *>(positions), nodes, count, out_mean, &used,
+                 (cudaStream_t)cuda_stream);
+    if (st == SNAP_OK && out_used) *out_used = used;
+    if (st == SNAP_OK) h->mark_use((cudaStream_t)cuda_stream);
+    return st;
+}
+
 snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions, float *scratch_positions,
                                  int32_t neg_samples, const snap_schedule *schedule, uint64_t seed, double tolerance,
                                  int32_t *chosen_segment, int32_t *chosen_block, double *chosen_ms,
-                                 double *chosen_objective, void *cuda_stream) {
+                                 double *chosen_objective, double *chosen_np, void *cuda_stream) {
     NvtxRange nvtx_range("snap_layout_autotune");
     if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
     if (h->opts.mode == SNAP_MODE_SYNC) return fail(SNAP_ERR_NOT_SUPPORTED, "autotuning applies to the HOGWILD modes");
@@ -1232,6 +1333,28 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     const bool exact = h->num_graphs > 1 || h->n <= 16384;
     const int64_t pairs = 16 << 20;
     const uint64_t pair_seed = seed ^ 0x5bd1e9955bd1e995ull;
+    // NP half of the gate (Section 4.1, r = 2) when the handle keeps its CSR
+    // and every graph fits the device NP kernel: 1,024 vertices drawn from
+    // the seed, the same for every candidate
+    bool np_on = gate && h->d_row_ptr && h->d_col;
+    if (np_on) {
+        int32_t max_graph = h->n;
+        if (h->num_graphs > 1) {
+            max_graph = 0;
+            for (const GraphInfo &gi : h->h_graphs) max_graph = gi.n > max_graph ? gi.n : max_graph;
+        }
+        np_on = max_graph <= kNpMaxGraph;
+    }
+    std::vector<int32_t> np_nodes;
+    if (np_on) {
+        np_nodes.resize(1024);
+        for (size_t q = 0; q < np_nodes.size(); ++q)
+            np_nodes[q] = (int32_t)(mix64(seed ^ (0x4E50ull << 32) ^ (uint64_t)q) % (uint64_t)h->n);
+    }
+    auto layout_np = [&](double *npv) -> snap_status {
+        int32_t used = 0;
+        return np_impl(h, scratch, np_nodes.data(), (int32_t)np_nodes.size(), npv, &used, stream);
+    };
     auto layout_objective = [&](const TuneCandidate &c, double *u) -> snap_status {
         cudaError_t e = apply_config(h, ac, c.target, c.block, stream);
         if (e == cudaSuccess) resident_grid(h, neg_samples);
@@ -1250,22 +1373,30 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
         return s2;
     };
     TuneCandidate best = cand.front();
-    double best_u = NAN;
+    double best_u = NAN, best_np = NAN;
     if (gate && !(best.target == entry.target && best.block == entry.block)) {
-        double u_ref = 0.0;
+        double u_ref = 0.0, np_ref = NAN;
         st = layout_objective(entry, &u_ref);
+        if (st == SNAP_OK && np_on) st = layout_np(&np_ref);
         for (const TuneCandidate &c : cand) {
             if (st != SNAP_OK) break;
             if (c.target == entry.target && c.block == entry.block) {
                 best = c;
                 best_u = u_ref;
+                best_np = np_ref;
                 break;
             }
-            double u = 0.0;
+            double u = 0.0, npv = NAN;
             st = layout_objective(c, &u);
-            if (st == SNAP_OK && std::isfinite(u) && u <= u_ref * (1.0 + tolerance)) {
+            bool pass = st == SNAP_OK && std::isfinite(u) && u <= u_ref * (1.0 + tolerance);
+            if (pass && np_on) {
+                st = layout_np(&npv);
+                pass = st == SNAP_OK && npv >= np_ref * (1.0 - tolerance);
+            }
+            if (pass) {
                 best = c;
                 best_u = u;
+                best_np = npv;
                 break;
             }
             if (st == SNAP_ERR_NUMERIC) st = SNAP_OK;   // a candidate that diverged is rejected
@@ -1276,6 +1407,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
         }
     } else if (gate) {
         st = layout_objective(best, &best_u);
+        if (st == SNAP_OK && np_on) st = layout_np(&best_np);
         if (st != SNAP_OK) return st;
     }
     err = apply_config(h, ac, best.target, best.block, stream);
@@ -1288,6 +1420,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     if (chosen_block) *chosen_block = h->block;
     if (chosen_ms) *chosen_ms = best.ms;
     if (chosen_objective) *chosen_objective = best_u;
+    if (chosen_np) *chosen_np = best_np;
     return snap_layout_check(h, cuda_stream);
 }
 
@@ -1440,6 +1573,7 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
         jd.nnz = h->act_nnz;
         jd.seg_len = h->act_seg_len;
         jd.alias = h->d_alias;
+        jd.narrow = h->act_narrow ? 1 : 0;
         jd.seg_prefix = total;
         jd.seed = seeds[q];
         jd.n = h->n;

@@ -164,6 +164,17 @@ __device__ __forceinline__ void later_negatives(const OrientedArgs &a, const Gra
     }
 }
 
+// The CSR indices of an entry's two directed copies (i, j) and (j, i).
+__device__ __forceinline__ void entry_edges(const OrientedArgs &a, int4 ent, int64_t &e1, int64_t &e2) {
+    if (a.narrow) {
+        e1 = (int64_t)(uint32_t)ent.y;
+        e2 = (int64_t)(uint32_t)ent.z;
+    } else {
+        e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
+        e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
+    }
+}
+
 template <bool RED, int G, bool W, bool E>
 __device__ __forceinline__ void oriented_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, int32_t j,
                                                int64_t e1, int64_t e2, float2 &yi, float &en) {
@@ -317,15 +328,15 @@ __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t sl
             yi0 = yi;
         }
 #if SNAP_ENT_PREFETCH
-        const int4 ent = ent_next;   // {j, indices of (i, j) and (j, i): low bits, bits 32..47}
+        const int4 ent = ent_next;   // {j, indices of (i, j) and (j, i), source or their high bits}
         if (p + 1 < p1) ent_next = load_entry(ep + step);
         if (!c.active) continue;
 #else
         if (!c.active) continue;
-        const int4 ent = load_entry(ep);   // {j, indices of (i, j) and (j, i): low bits, bits 32..47}
+        const int4 ent = load_entry(ep);   // {j, indices of (i, j) and (j, i), source or their high bits}
 #endif
-        const int64_t e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
-        const int64_t e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
+        int64_t e1, e2;
+        entry_edges(a, ent, e1, e2);
         oriented_entry<RED, G, W, E>(a, c, row, ent.x, e1, e2, yi, en);
     }
     if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
@@ -355,8 +366,8 @@ template <int G>
 __device__ __forceinline__ void stage_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, int4 ent,
                                             StagedEntry &st) {
     st.j = ent.x;
-    const int64_t e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
-    const int64_t e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
+    int64_t e1, e2;
+    entry_edges(a, ent, e1, e2);
     if (G > 0) {
         const uint4 w1 = words_in(c, e1, 0u);
         const uint4 w2 = words_in(c, e2, 0u);
@@ -409,8 +420,11 @@ __device__ __forceinline__ void finish_entry(const OrientedArgs &a, float eta, i
             negative_group<RED, E>(a.pos, eta, st.s2, st.v2, G, yj, i, yi, en);
         }
     }
-    apply_partner<RED>(a.pos, st.j, yj, make_float2(yj.x - yj0.x, yj.y - yj0.y));
-    st.yj = yj;
+    const float2 dj = make_float2(__fsub_rn(yj.x, yj0.x), __fsub_rn(yj.y, yj0.y));
+    apply_partner<RED>(a.pos, st.j, yj, dj);
+    // what memory holds for j after this lane's write: the exchanged value, or
+    // the gathered value plus the added change (rounded twice)
+    st.yj = RED ? make_float2(__fadd_rn(yj0.x, dj.x), __fadd_rn(yj0.y, dj.y)) : yj;
 }
 
 // The value this lane last wrote for vertex x while finishing entry `done`
@@ -446,7 +460,9 @@ __device__ __forceinline__ float2 written_source(const OrientedArgs &a, float2 y
     if (!RED) return yi;
     const float together = (float)pieces * a.inflight_share;
     const float inv = together > 1.0f ? 1.0f / together : 1.0f;
-    return make_float2(yi0.x + (yi.x - yi0.x) * inv, yi0.y + (yi.y - yi0.y) * inv);
+    // the operand write_oriented_source adds, then the addition memory performs
+    return make_float2(__fadd_rn(yi0.x, __fmul_rn(__fsub_rn(yi.x, yi0.x), inv)),
+                       __fadd_rn(yi0.y, __fmul_rn(__fsub_rn(yi.y, yi0.y), inv)));
 }
 
 template <bool RED, int G, bool MULTI, bool E>
@@ -513,6 +529,103 @@ __device__ __forceinline__ void oriented_chunk_pipe(const OrientedArgs &a, int64
                                              flags);
 }
 
+// ---------------------------------------------------------------------------
+// Direct chunk walk (the default for single graphs with uniform negatives,
+// k <= 4 and narrow entries).  Every entry names its source, so a lane needs
+// no row offsets: the first entry of a chunk gives the row, and a change of
+// source in a later entry is a row change.  The walk is pipelined as
+// oriented_chunk_pipe (the next entry's words drawn and its gathers issued
+// before the current entry's updates, with forwarding of the lane's own
+// writes), and the kernel loop below also loads the lane's next chunk's first
+// entry and slot descriptor before it walks the current one, so the stream's
+// latency is hidden too.  HOGWILD_RED reads the row's piece count (the chunks
+// the row spans) when the row starts, for the write-back's scaling.
+// SNAP_DIRECT = 0 (build switch) keeps the row-offset walks for every case.
+// ---------------------------------------------------------------------------
+#ifndef SNAP_DIRECT
+#define SNAP_DIRECT 1
+#endif
+
+template <bool RED, int G>
+__device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, const GraphCtx &c, int64_t slot,
+                                                      int4 ent0, int2 mt, uint32_t &flags) {
+    const int64_t step = chunk_group_width(slot, a.num_segs);
+    const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
+    const int64_t first = (int64_t)mt.y * a.seg_len;
+    const int32_t len = (int32_t)(a.nnz - first < (int64_t)a.seg_len ? a.nnz - first : (int64_t)a.seg_len);
+    float en = 0.0f;
+    int32_t row = ent0.w;
+    float2 yi = load_pos(a.pos + row);
+    int32_t pieces = RED ? __ldg(a.pieces + row) : 1;
+    StagedEntry cur, nxt;
+    stage_entry<G>(a, c, row, ent0, cur);
+    int4 ent_next = len > 1 ? load_entry(ep + step) : ent0;
+    float2 yi0 = yi;
+    for (int32_t q = 0; q < len; ++q) {
+        const bool more = q + 1 < len;
+        int32_t row_n = row, pieces_n = pieces;
+        float2 yi_n = yi;
+        if (more) {
+            row_n = ent_next.w;
+            if (row_n != row) {
+                yi_n = load_pos(a.pos + row_n);
+                if (RED) pieces_n = __ldg(a.pieces + row_n);
+            }
+            stage_entry<G>(a, c, row_n, ent_next, nxt);
+            if (q + 2 < len) ent_next = load_entry(ep + (int64_t)(q + 2) * step);
+        }
+        finish_entry<RED, G, false>(a, c.eta, row, cur, yi, en);
+        if (!more) break;
+        if (row_n != row) {
+            write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
+            const float2 mem = written_source<RED>(a, yi, yi0, pieces);
+            yi_n = forwarded<G>(row_n, yi_n, cur, row, mem);
+            forward_into<G>(nxt, cur, row, mem);
+            row = row_n;
+            yi = yi_n;
+            yi0 = yi;
+            pieces = pieces_n;
+        } else {
+            forward_into<G>(nxt, cur, row, yi);
+        }
+        cur = nxt;
+    }
+    write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
+}
+
+// The lanes' slot loop of the direct walk: the next chunk's first entry and
+// descriptor are in flight while the current chunk is walked.
+template <bool RED, int G>
+__device__ __forceinline__ void direct_slots(const OrientedArgs &a, uint32_t &flags) {
+    const int64_t groups = (a.num_segs + 31) >> 5;
+    const int64_t limit = groups << 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const GraphCtx c = graph_ctx<false>(a, 0);
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t ws = w < limit ? slot_of(w, groups, a.perm_mul, a.perm_add) : a.num_segs;
+    int4 ent0 = make_int4(0, 0, 0, 0);
+    int2 mt = make_int2(0, 0);
+    if (ws < a.num_segs) {
+        ent0 = load_entry(a.ent + chunk_entry_index(ws, a.num_segs, a.seg_len, 0));
+        mt = __ldg(a.meta + ws);
+    }
+    while (w < limit) {
+        const int64_t w2 = w + stride;
+        const int64_t ws2 = w2 < limit ? slot_of(w2, groups, a.perm_mul, a.perm_add) : a.num_segs;
+        int4 ent2 = make_int4(0, 0, 0, 0);
+        int2 mt2 = make_int2(0, 0);
+        if (ws2 < a.num_segs) {
+            ent2 = load_entry(a.ent + chunk_entry_index(ws2, a.num_segs, a.seg_len, 0));
+            mt2 = __ldg(a.meta + ws2);
+        }
+        if (ws < a.num_segs) oriented_chunk_direct<RED, G>(a, c, ws, ent0, mt, flags);
+        w = w2;
+        ws = ws2;
+        ent0 = ent2;
+        mt = mt2;
+    }
+}
+
 // In a batch a chunk may cross from one graph into the next; the graph is
 // looked up again at every row change.  E: also sum the actual energy of the
 // epoch (half the sum over the directed steps of U^a and over the drawn pairs
@@ -521,6 +634,11 @@ template <bool RED, int G, bool MULTI, bool W, bool E>
 __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_kernel(const OrientedArgs a) {
     uint32_t flags = 0;
     double energy = 0.0;
+    if (SNAP_DIRECT && !MULTI && !W && !E && a.narrow && a.k <= 4 && (!RED || a.pieces)) {
+        direct_slots<RED, G>(a, flags);
+        if (flags) atomicOr(a.status, flags);
+        return;
+    }
     const int64_t groups = (a.num_segs + 31) >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // a multiple of 32
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (groups << 5); w += stride) {
@@ -585,6 +703,8 @@ __global__ void __launch_bounds__(256, SNAP_MULTI_MIN_BLOCKS) multi_epoch_kernel
         a.inflight_share = m.inflight_share;
         a.alias = jd.alias;
         a.energy = nullptr;
+        a.narrow = jd.narrow;
+        a.pieces = nullptr;
         float en = 0.0f;
         if (WEIGHTED && G > 0 && a.alias)
             oriented_chunk<RED, G, false, true, false>(a, ws - jd.seg_prefix, flags, en);

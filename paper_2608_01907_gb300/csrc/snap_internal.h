@@ -121,6 +121,8 @@ struct OrientedArgs {
     float inflight_share;        // lanes in flight / slots (share of the chunks running at once)
     const uint2 *alias;          // weighted negatives (alias table, graph-local ids); null: uniform
     double *energy;              // actual energy of the epoch is added here (null: not computed)
+    int32_t narrow;              // entries {j, (i, j), (j, i), i}: 32-bit edge indices, the source in .w
+    const int32_t *pieces;       // narrow lists: chunks each vertex's oriented row spans (HOGWILD_RED)
 };
 
 // Dispatches on a.alias (weighted negatives, epoch_weighted.cu) and a.energy
@@ -148,6 +150,7 @@ struct JobDesc {
     float eta;
     int32_t seg_len;
     const uint2 *alias;     // the job's alias table, or null (uniform)
+    int32_t narrow;         // the job's entry format (OrientedArgs::narrow)
 };
 
 struct MultiArgs {
@@ -191,7 +194,9 @@ cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in
                                cudaStream_t s);
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                   const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  cudaStream_t s);
+                                  int narrow, cudaStream_t s);
+// pieces[v] = chunks of T entries that v's oriented row spans.
+cudaError_t launch_row_pieces(const int64_t *act_rp, int32_t n, int32_t T, int32_t *pieces, cudaStream_t s);
 cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,
                                  cudaStream_t s);
 // Moves the oriented entries from layout `from` (T == 0: plain row-major) to
@@ -215,6 +220,14 @@ cudaError_t launch_objective_pairs_exact(const float2 *pos, const int32_t *deg, 
 cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, const float4 *wt,
                                          const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
                                          double *partial, int grid, cudaStream_t s);
+// Neighbourhood preservation (Section 4.1, r = 2) of `count` sampled
+// vertices: out[q] = the Jaccard index of the 2-hop set and the nearest set
+// of nodes[q], or -1 for a vertex without neighbours.  Every graph (all of
+// [0, n) when graphs is null) has at most max_graph vertices.
+constexpr int32_t kNpMaxGraph = 1 << 18;
+cudaError_t launch_np_samples(const int64_t *row_ptr, const int32_t *col_idx, const float2 *pos, const int32_t *nodes,
+                              int32_t count, const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
+                              int32_t max_graph, double *out, int grid, cudaStream_t s);
 cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, const float4 *wt, int32_t n,
                                            int64_t pairs, uint64_t seed, double *partial, int grid,
                                            cudaStream_t s);

@@ -78,7 +78,7 @@ def main():
                 "# Written by tests/golden/make_convergence_lfr.py.\n"
                 "# T si np oracle_seconds\n")
         for T, si, npv, secs in rows:
-            f.write(f"{T} {si!r} {npv!r} {secs:.0f}\n")
+            f.write(f"{T} {float(si)!r} {float(npv)!r} {secs:.0f}\n")
     print(open(OUT).read())
 
 

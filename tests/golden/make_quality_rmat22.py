@@ -104,7 +104,7 @@ def main():
                 "# Written by tests/golden/make_quality_rmat22.py.\n"
                 "# seed objective np hub_offset oracle_seconds\n")
         for seed, ob, npv, hub, secs in rows:
-            f.write(f"{seed} {ob!r} {npv!r} {hub!r} {secs:.0f}\n")
+            f.write(f"{seed} {float(ob)!r} {float(npv)!r} {float(hub)!r} {secs:.0f}\n")
     print(open(OUT).read())
 
 

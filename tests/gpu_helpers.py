@@ -114,3 +114,10 @@ def coordinate_error(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
     gpu = np.asarray(gpu, dtype=np.float64)
     scale = max(float(np.sqrt((ref ** 2).mean())), 1e-30)
     return (np.abs(gpu - ref) / np.maximum(np.abs(ref), scale)).max(axis=1)
+
+
+def rmat25_bfs():
+    """A graph whose positions exceed L2: R-MAT 2^25 / 268,435,456 undirected
+    edges from the native generator (seed 1), BFS locality relabelling."""
+    from synth import bfs_relabel, rmat_graph_native
+    return cached_graph("rmat25_268m_native_bfs", lambda: bfs_relabel(rmat_graph_native(25, 268_435_456, seed=1)))
