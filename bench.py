@@ -134,7 +134,8 @@ def probe_rates(nbytes, stream):
     """Hardware ceilings measured now on an array of `nbytes` (the size of the
     position array): L2 streaming read bandwidth (bytes/s; the array fits in
     L2), random 8-byte loads/s and random 8-byte vector atomic adds/s, each
-    alone (bench_probe.cu).  Best of two runs each."""
+    alone, and the two interleaved without dependence (pairs/s)
+    (bench_probe.cu).  Best of two runs each."""
     import ctypes
     import torch
     lib = probe_library()
@@ -144,7 +145,8 @@ def probe_rates(nbytes, stream):
     sms = torch.cuda.get_device_properties(buf.device).multi_processor_count
     out = {}
     for name, op, iters, grid in (("l2_read_bytes_per_s", 0, 16, sms * 8), ("random_loads_per_s", 1, 16, sms * 8),
-                                  ("random_atomic_adds_per_s", 2, 16, sms * 8)):
+                                  ("random_atomic_adds_per_s", 2, 16, sms * 8),
+                                  ("random_load_atomic_pairs_per_s", 3, 16, sms * 8)):
         best = 0.0
         for _ in range(2):
             r = lib.bench_probe_rate(ctypes.c_void_p(buf.data_ptr()), nbytes, op, iters, grid,
@@ -331,6 +333,13 @@ def rooflines(nnz, n, k, launch_ms, probes, peak_hbm, peak_kind, traffic, kernel
                "bound_ms": t_bound * 1e3, "frac": t_bound / launch_s,
                "binding": "atomic adds" if t_add >= t_load else "loads",
                "note": "random 8-byte loads and vector float atomic adds, each probed alone (bench_probe.cu ops 1-2)"}
+        if not sync and probes.get("random_load_atomic_pairs_per_s"):
+            t_mix = n_ops / probes["random_load_atomic_pairs_per_s"]
+            ops["mixed_pair_peak_per_s"] = probes["random_load_atomic_pairs_per_s"]
+            ops["mixed_bound_ms"] = t_mix * 1e3
+            ops["mixed_frac"] = t_mix / launch_s
+            ops["mixed_note"] = ("the same loads and atomic adds interleaved without dependence (bench_probe.cu op 3): "
+                                 "the ceiling of this access mix")
     binding = hbm
     if l2 and l2_bytes / (l2["peak"] * 1e9) > hbm_bytes / (peak_hbm * 1e9):
         binding = l2
@@ -632,7 +641,7 @@ def batch_result(args, local_rank, steps, warmup):
     # block size come from the autotuner, gated at 2% of the default's objective
     h = snap.snap_layout_create_batch(rp, ci, offs, snap.make_options(cuda_graph=True, keep_csr=True), stream)
     t_tune = time.perf_counter()
-    seg, blk, tune_ms, tune_u, tune_np = snap.snap_layout_autotune(h, Y, k, sched, args.seed, Y0_d, 0.02, stream)
+    seg, blk, tune_ms, tune_u, tune_np, tune_order = snap.snap_layout_autotune(h, Y, k, sched, args.seed, Y0_d, 0.02, stream)
     t_tune = time.perf_counter() - t_tune
 
     def step():
@@ -692,7 +701,8 @@ def batch_result(args, local_rank, steps, warmup):
             "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "config": {"workload": f"batch-sbm-{offs.size - 1}-graphs-k{k}-{EPOCHS}ep", "graphs": int(offs.size - 1),
                        "n_total": n, "undirected_edges": nnz // 2, "mode": "hogwild_red",
-                       "autotuned": {"chunk_entries": seg, "block": blk, "ms_per_epoch": tune_ms,
+                       "autotuned": {"chunk_entries": seg, "block": blk,
+                                     "row_order": "ascending" if tune_order else "affine", "ms_per_epoch": tune_ms,
                                      "objective": tune_u, "np": tune_np, "seconds": t_tune, "tolerance": 0.02,
                                      "gate": "objective (Eq. 4) and NP (Section 4.1) within 2% of the default "
                                              "configuration's layout"},

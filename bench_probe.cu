@@ -14,6 +14,10 @@
 //   op 2  random atomic adds: 8-byte vector float adds without return
 //         (red.global.add.v2.f32) to uniformly random slots, 8 per thread per
 //         iteration; atomics per second
+//   op 3  the two mixed: per thread and iteration 8 random loads and 8
+//         random atomic adds to other slots, independent of each other (the
+//         mix the epoch kernels issue, without their dependence); load +
+//         atomic pairs per second
 // Slots come from a 64-bit mixing hash of (thread, iteration) reduced to
 // [0, n) by a multiply-shift, so every access stays inside the array.
 #include <cuda_runtime.h>
@@ -69,6 +73,25 @@ __global__ void __launch_bounds__(256) random_red_kernel(float2 *a, uint32_t n, 
     }
 }
 
+__global__ void __launch_bounds__(256) random_mixed_kernel(float2 *a, uint32_t n, int iters, float *sink) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    for (int it = 0; it < iters; ++it) {
+        float2 v[kDepth];
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) v[d] = __ldcg(a + mix_slot((tid << 24) ^ ((uint64_t)it * kDepth + d), n));
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) {
+            float2 *p = a + mix_slot(((tid << 24) ^ ((uint64_t)it * kDepth + d)) + 0x9E37ull, n);
+            asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(1e-7f), "f"(0.0f)
+                         : "memory");
+        }
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) acc += v[d].x;
+    }
+    if (acc == 12345.678f) sink[0] = acc;
+}
+
 }  // namespace
 
 // Runs probe `op` (above) on the caller's device array `a` of `bytes` bytes
@@ -78,7 +101,7 @@ __global__ void __launch_bounds__(256) random_red_kernel(float2 *a, uint32_t n, 
 // otherwise) or a negative value on error.
 extern "C" double bench_probe_rate(float *a, int64_t bytes, int op, int iters, int grid, float *sink,
                                    void *cuda_stream) {
-    if (!a || !sink || bytes < 32 || (bytes & 15) != 0 || op < 0 || op > 2 || iters <= 0 || grid <= 0) return -1.0;
+    if (!a || !sink || bytes < 32 || (bytes & 15) != 0 || op < 0 || op > 3 || iters <= 0 || grid <= 0) return -1.0;
     const int64_t n2 = bytes / 8;
     if (n2 > 0xFFFFFFFFll) return -1.0;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -95,8 +118,10 @@ extern "C" double bench_probe_rate(float *a, int64_t bytes, int op, int iters, i
             stream_read_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(a), bytes / 16, iters, sink);
         else if (op == 1)
             random_load_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(a), (uint32_t)n2, iters, sink);
-        else
+        else if (op == 2)
             random_red_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<float2 *>(a), (uint32_t)n2, iters);
+        else
+            random_mixed_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<float2 *>(a), (uint32_t)n2, iters, sink);
         err = cudaGetLastError();
     }
     cudaEventRecord(e1, s);

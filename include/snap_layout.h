@@ -134,6 +134,11 @@ typedef struct {
  * snap_layout_neighborhood_preservation and the NP half of the autotuner's
  * gate; snap_layout_device_bytes counts it. */
 #define SNAP_FLAG_KEEP_CSR 2
+/* snap_options.flags: store each oriented row's entries in ascending partner
+ * id instead of the default affine order (which keeps entries of nearby
+ * partners apart, Section 3.4's shuffle; the ascending order gathers
+ * neighbouring partners back to back).  The autotuner may switch it. */
+#define SNAP_FLAG_ASCENDING_ROWS 4
 
 /* Fill *opts with the defaults (HOGWILD_RED, UNIFORM, S = 1, no cap). */
 void snap_options_default(snap_options *opts);
@@ -296,7 +301,8 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
  * has on entry.  The choice stays on the handle.
  *
  * Candidates: the entry configuration and 4, 8, 16, 32 entries x 128/256
- * threads.  Longer chunks apply more of one source's steps back to back,
+ * threads x the two row orders (affine, ascending partner id;
+ * SNAP_FLAG_ASCENDING_ROWS).  Longer chunks apply more of one source's steps back to back,
  * which is faster but moves the visiting order away from Algorithm 1's
  * shuffled order and can cost energy (Section 3.4's lock-free scheme
  * bounds concurrency, not order).
@@ -323,7 +329,8 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
  *                      tolerance < 0).
  *   scratch_positions  device, n x 2 float32; overwritten.
  *   neg_samples, schedule, seed   as for snap_layout_epochs.
- *   chosen_segment, chosen_block, chosen_ms (ms per epoch),
+ *   chosen_segment, chosen_block, chosen_row_order (0 affine, 1 ascending),
+ *   chosen_ms (ms per epoch),
  *   chosen_objective (U of the chosen layout; NaN without the gate),
  *   chosen_np (NP of the chosen layout; NaN when NP is not gated)
  *                      host outputs, nullable.
@@ -334,8 +341,8 @@ int64_t snap_layout_device_bytes(snap_layout_t h);
 snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions, float *scratch_positions,
                                  int32_t neg_samples, const snap_schedule *schedule, uint64_t seed,
                                  double tolerance, int32_t *chosen_segment, int32_t *chosen_block,
-                                 double *chosen_ms, double *chosen_objective, double *chosen_np,
-                                 void *cuda_stream);
+                                 int32_t *chosen_row_order, double *chosen_ms, double *chosen_objective,
+                                 double *chosen_np, void *cuda_stream);
 
 /*
  * snap_layout_neighborhood_preservation -- NP of a layout (Section 4.1,

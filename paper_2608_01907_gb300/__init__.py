@@ -53,6 +53,7 @@ class SnapOptions(ctypes.Structure):
 
 FLAG_CUDA_GRAPH = 1
 FLAG_KEEP_CSR = 2
+FLAG_ASCENDING_ROWS = 4
 
 
 def linear_schedule(eta0: float = 1.0, total_epochs: int = 30, eta_min: float | None = None,
@@ -98,7 +99,7 @@ def load_library():
     lib.snap_layout_objective.restype = st
     lib.snap_layout_check.argtypes = [P, P]
     lib.snap_layout_check.restype = st
-    lib.snap_layout_autotune.argtypes = [P, P, P, i32, P, u64, f64, P, P, P, P, P, P]
+    lib.snap_layout_autotune.argtypes = [P, P, P, i32, P, u64, f64, P, P, P, P, P, P, P]
     lib.snap_layout_neighborhood_preservation.argtypes = [P, P, P, i32, P, P, P]
     lib.snap_layout_neighborhood_preservation.restype = st
     lib.snap_layout_autotune.restype = st
@@ -176,13 +177,14 @@ def snap_options_default() -> SnapOptions:
 def make_options(mode: int = MODE_HOGWILD_RED, sync_substeps: int = 1, sync_cap: float = 0.0,
                  segment_edges: int = 0, block_threads: int = 0, sampler: int = SAMPLER_UNIFORM,
                  cuda_graph: bool = False, max_inflight: float = 0.0, node_weights=None,
-                 keep_csr: bool = False) -> SnapOptions:
+                 keep_csr: bool = False, ascending_rows: bool = False) -> SnapOptions:
     """Options for snap_layout_create; node_weights (n floats) goes with SAMPLER_WEIGHTS
     and is kept alive by the returned object."""
     o = snap_options_default()
     o.mode, o.sync_substeps, o.sync_cap = mode, sync_substeps, sync_cap
     o.segment_edges, o.block_threads, o.sampler = segment_edges, block_threads, sampler
-    o.flags = (FLAG_CUDA_GRAPH if cuda_graph else 0) | (FLAG_KEEP_CSR if keep_csr else 0)
+    o.flags = ((FLAG_CUDA_GRAPH if cuda_graph else 0) | (FLAG_KEEP_CSR if keep_csr else 0)
+               | (FLAG_ASCENDING_ROWS if ascending_rows else 0))
     o.max_inflight = max_inflight
     if node_weights is not None:
         w = _host(node_weights, np.float32)
@@ -257,18 +259,20 @@ def snap_layout_check(h, stream=None) -> None:
 
 def snap_layout_autotune(h, scratch_positions, neg_samples: int, schedule: SnapSchedule, seed: int,
                          initial_positions=None, tolerance: float = 0.02, stream=None):
-    """Returns (chunk entries, block threads, ms per epoch, objective, NP) chosen
-    for the handle; tolerance < 0 (or no initial positions) times the candidates
-    only.  NP is NaN unless the handle keeps its CSR (keep_csr)."""
+    """Returns (chunk entries, block threads, ms per epoch, objective, NP, row
+    order) chosen for the handle; tolerance < 0 (or no initial positions) times
+    the candidates only.  NP is NaN unless the handle keeps its CSR
+    (keep_csr); row order 0 is the affine order, 1 ascending partner id."""
     if initial_positions is None:
         tolerance = -1.0
-    seg, blk, ms, u, npv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    seg, blk, order = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms, u, npv = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     init = _device_positions(initial_positions) if initial_positions is not None else None
     _check(load_library().snap_layout_autotune(h, init, _device_positions(scratch_positions), neg_samples,
                                                ctypes.byref(schedule), seed, tolerance, ctypes.byref(seg),
-                                               ctypes.byref(blk), ctypes.byref(ms), ctypes.byref(u),
-                                               ctypes.byref(npv), _stream(stream)))
-    return seg.value, blk.value, ms.value, u.value, npv.value
+                                               ctypes.byref(blk), ctypes.byref(order), ctypes.byref(ms),
+                                               ctypes.byref(u), ctypes.byref(npv), _stream(stream)))
+    return seg.value, blk.value, ms.value, u.value, npv.value, order.value
 
 
 def snap_layout_neighborhood_preservation(h, positions, nodes, stream=None):

@@ -317,11 +317,12 @@ static int64_t golden_multiplier(int64_t m) {
 // (Re)cuts the oriented list into chunks of `target` entries: the entries
 // move from the current layout (row-major right after construction) into a
 // fresh array in the new slot order, and the slot table is rebuilt.
-static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, cudaStream_t stream) {
+static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, int32_t order, cudaStream_t stream) {
     if (h->act_nnz > 0 && target > h->act_nnz) target = (int32_t)h->act_nnz;   // one chunk
     if (h->last_use) cudaStreamWaitEvent(stream, h->last_use, 0);   // the old arrays' last readers
     ChunkLayout to;
     to.T = target;
+    to.order = order;
     to.S = (h->act_nnz + target - 1) / target;
     to.mul = golden_multiplier(to.S);
     to.add = to.S > 1 ? to.S / 3 : 0;
@@ -433,9 +434,9 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     if (total != h->act_nnz)
         return fail(SNAP_ERR_CUDA, "orientation produced %lld entries, expected %lld", (long long)total,
                     (long long)h->act_nnz);
-    h->act_layout = ChunkLayout{0, 0, 0, 0};   // row-major
+    h->act_layout = ChunkLayout{0, 0, 0, 0};   // row-major, rows in the affine order of the scatter
     h->act_ent_bytes = 0;
-    err = set_chunks(h, ac, h->act_seg_len, stream);
+    err = set_chunks(h, ac, h->act_seg_len, (h->opts.flags & SNAP_FLAG_ASCENDING_ROWS) ? 1 : 0, stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
     if (err != cudaSuccess) return cuda_fail(err, "oriented chunks");
     if (!(h->opts.flags & SNAP_FLAG_KEEP_CSR)) {
@@ -498,7 +499,7 @@ static snap_status check_options(const snap_options &o) {
     if (o.segment_edges != 0 && (o.segment_edges < 4 || o.segment_edges > 4096 || o.segment_edges % 4 != 0))
         return fail(SNAP_ERR_INVALID_ARG, "segment_edges = %d must be 0 or a multiple of 4 in [4, 4096]",
                     o.segment_edges);
-    if (o.flags & ~(SNAP_FLAG_CUDA_GRAPH | SNAP_FLAG_KEEP_CSR))
+    if (o.flags & ~(SNAP_FLAG_CUDA_GRAPH | SNAP_FLAG_KEEP_CSR | SNAP_FLAG_ASCENDING_ROWS))
         return fail(SNAP_ERR_INVALID_ARG, "unknown flags 0x%x", o.flags);
     if (!(o.max_inflight >= 0.0f) || !(o.max_inflight <= 1.0f))
         return fail(SNAP_ERR_INVALID_ARG, "max_inflight must be in [0, 1]");
@@ -1160,15 +1161,15 @@ int64_t snap_layout_device_bytes(snap_layout_t h) { return h ? h->device_bytes :
 
 // One candidate configuration of the autotuner.
 struct TuneCandidate {
-    int32_t target, block;
+    int32_t target, block, order;
     double ms;
 };
 
-// Puts a (chunk size, block) configuration on the handle.
-static cudaError_t apply_config(snap_layout *h, AllocCounter &ac, int32_t target, int32_t block,
+// Puts a (chunk size, block, row order) configuration on the handle.
+static cudaError_t apply_config(snap_layout *h, AllocCounter &ac, int32_t target, int32_t block, int32_t order,
                                 cudaStream_t stream) {
-    if (target != h->act_seg_len) {
-        const cudaError_t err = set_chunks(h, ac, target, stream);
+    if (target != h->act_seg_len || order != h->act_layout.order) {
+        const cudaError_t err = set_chunks(h, ac, target, order, stream);
         if (err != cudaSuccess) return err;
     }
     h->block = block;
@@ -1256,8 +1257,9 @@ snap_status snap_layout_neighborhood_preservation(snap_layout_t h, const float *
 
 snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions, float *scratch_positions,
                                  int32_t neg_samples, const snap_schedule *schedule, uint64_t seed, double tolerance,
-                                 int32_t *chosen_segment, int32_t *chosen_block, double *chosen_ms,
-                                 double *chosen_objective, double *chosen_np, void *cuda_stream) {
+                                 int32_t *chosen_segment, int32_t *chosen_block, int32_t *chosen_row_order,
+                                 double *chosen_ms, double *chosen_objective, double *chosen_np,
+                                 void *cuda_stream) {
     NvtxRange nvtx_range("snap_layout_autotune");
     if (!h) return fail(SNAP_ERR_INVALID_ARG, "handle is NULL");
     if (h->opts.mode == SNAP_MODE_SYNC) return fail(SNAP_ERR_NOT_SUPPORTED, "autotuning applies to the HOGWILD modes");
@@ -1280,10 +1282,13 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     const int32_t gate_epochs = sched.total_epochs;
 
     // the configuration at entry is always a candidate and the gate's reference
-    std::vector<TuneCandidate> cand{{h->act_seg_len, h->block, 0.0}};
-    for (int32_t target : {4, 8, 16, 32})
-        for (int32_t block : {128, 256})
-            if (target != h->act_seg_len || block != h->block) cand.push_back({target, block, 0.0});
+    const int32_t entry_order = h->act_layout.order;
+    std::vector<TuneCandidate> cand{{h->act_seg_len, h->block, entry_order, 0.0}};
+    for (int32_t order : {0, 1})
+        for (int32_t target : {4, 8, 16, 32})
+            for (int32_t block : {128, 256})
+                if (target != h->act_seg_len || block != h->block || order != entry_order)
+                    cand.push_back({target, block, order, 0.0});
 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     AllocCounter ac;
@@ -1295,7 +1300,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     for (TuneCandidate &c : cand) c.ms = 1e300;
     for (int pass = 0; pass < 2 && err == cudaSuccess; ++pass) {
         for (TuneCandidate &c : cand) {
-            err = apply_config(h, ac, c.target, c.block, stream);
+            err = apply_config(h, ac, c.target, c.block, c.order, stream);
             if (err == cudaSuccess) resident_grid(h, neg_samples);
             if (err == cudaSuccess && gate)
                 err = cudaMemcpyAsync(scratch, initial_positions, pos_bytes, cudaMemcpyDeviceToDevice, stream);
@@ -1314,7 +1319,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     if (e1) cudaEventDestroy(e1);
     if (err != cudaSuccess) {
         cudaGetLastError();
-        apply_config(h, ac, cand.front().target, cand.front().block, stream);
+        apply_config(h, ac, cand.front().target, cand.front().block, cand.front().order, stream);
         return cuda_fail(err, "autotune timing");
     }
     // a candidate replaces the entry configuration only if it is at least 3%
@@ -1356,7 +1361,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
         return np_impl(h, scratch, np_nodes.data(), (int32_t)np_nodes.size(), npv, &used, stream);
     };
     auto layout_objective = [&](const TuneCandidate &c, double *u) -> snap_status {
-        cudaError_t e = apply_config(h, ac, c.target, c.block, stream);
+        cudaError_t e = apply_config(h, ac, c.target, c.block, c.order, stream);
         if (e == cudaSuccess) resident_grid(h, neg_samples);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(scratch, initial_positions, pos_bytes, cudaMemcpyDeviceToDevice, stream);
@@ -1374,13 +1379,16 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     };
     TuneCandidate best = cand.front();
     double best_u = NAN, best_np = NAN;
-    if (gate && !(best.target == entry.target && best.block == entry.block)) {
+    auto same = [](const TuneCandidate &x, const TuneCandidate &y) {
+        return x.target == y.target && x.block == y.block && x.order == y.order;
+    };
+    if (gate && !same(best, entry)) {
         double u_ref = 0.0, np_ref = NAN;
         st = layout_objective(entry, &u_ref);
         if (st == SNAP_OK && np_on) st = layout_np(&np_ref);
         for (const TuneCandidate &c : cand) {
             if (st != SNAP_OK) break;
-            if (c.target == entry.target && c.block == entry.block) {
+            if (same(c, entry)) {
                 best = c;
                 best_u = u_ref;
                 best_np = np_ref;
@@ -1402,7 +1410,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
             if (st == SNAP_ERR_NUMERIC) st = SNAP_OK;   // a candidate that diverged is rejected
         }
         if (st != SNAP_OK) {
-            apply_config(h, ac, entry.target, entry.block, stream);
+            apply_config(h, ac, entry.target, entry.block, entry.order, stream);
             return st;
         }
     } else if (gate) {
@@ -1410,7 +1418,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
         if (st == SNAP_OK && np_on) st = layout_np(&best_np);
         if (st != SNAP_OK) return st;
     }
-    err = apply_config(h, ac, best.target, best.block, stream);
+    err = apply_config(h, ac, best.target, best.block, best.order, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(err, "autotune");
@@ -1418,6 +1426,7 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
     h->mark_use(stream);
     if (chosen_segment) *chosen_segment = h->act_seg_len;
     if (chosen_block) *chosen_block = h->block;
+    if (chosen_row_order) *chosen_row_order = h->act_layout.order;
     if (chosen_ms) *chosen_ms = best.ms;
     if (chosen_objective) *chosen_objective = best_u;
     if (chosen_np) *chosen_np = best_np;

@@ -153,11 +153,34 @@ __device__ __forceinline__ int64_t gcd_dev(int64_t a, int64_t b) {
     return a;
 }
 
-__device__ __forceinline__ int32_t row_position(int32_t q, int32_t L) {
-    if (L <= 2) return q;
+__device__ __forceinline__ int64_t row_multiplier(int32_t L) {
     int64_t a = (int64_t)(0.6180339887498949 * (double)L) | 1;
     while (gcd_dev(a, L) != 1) a += 2;
-    return (int32_t)((a * (int64_t)q) % L);
+    return a;
+}
+
+__device__ __forceinline__ int32_t row_position(int32_t q, int32_t L) {
+    if (L <= 2) return q;
+    return (int32_t)((row_multiplier(L) * (int64_t)q) % L);
+}
+
+// Rank (ascending partner id) of the entry stored at offset o of a row of
+// length L in the affine order: the inverse of row_position.
+__device__ __forceinline__ int32_t row_rank(int32_t o, int32_t L) {
+    if (L <= 2) return o;
+    // inverse of a mod L by the extended Euclidean algorithm
+    int64_t r0 = L, r1 = row_multiplier(L) % L, t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        const int64_t qt = r0 / r1;
+        int64_t tmp = r0 - qt * r1;
+        r0 = r1;
+        r1 = tmp;
+        tmp = t0 - qt * t1;
+        t0 = t1;
+        t1 = tmp;
+    }
+    const int64_t inv = t0 < 0 ? t0 + L : t0;
+    return (int32_t)((inv * (int64_t)o) % L);
 }
 
 __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
@@ -212,21 +235,33 @@ __global__ void chunk_layout_kernel(const int4 *__restrict__ src, const ChunkLay
             const int64_t c = p / from.T;
             q = chunk_entry_index(chunk_slot(from, c), from.S, from.T, p - c * from.T);
         }
-        const int64_t c = p / to.T;
-        const int64_t t = p - c * to.T;
-        const int64_t slot = chunk_slot(to, c);
-        dst[chunk_entry_index(slot, to.S, to.T, t)] = src[q];
-        if (t == 0) {
-            int32_t lo = 0, hi = n - 1;   // last row starting at or before p: the row holding p
+        // p is the entry's row-major index in `from`'s row order; pt its index
+        // in `to`'s (the same row, another place when the orders differ)
+        int64_t pt = p;
+        int32_t row = -1;
+        auto row_of = [&](int64_t x) {
+            int32_t lo = 0, hi = n - 1;   // last row starting at or before x: the row holding x
             while (lo < hi) {
                 const int32_t mid = lo + (hi - lo + 1) / 2;
-                if (act_rp[mid] <= p)
+                if (act_rp[mid] <= x)
                     lo = mid;
                 else
                     hi = mid - 1;
             }
-            meta[slot] = make_int2(lo, (int32_t)c);
+            return lo;
+        };
+        if (from.order != to.order) {
+            row = row_of(p);
+            const int64_t b = act_rp[row];
+            const int32_t L = (int32_t)(act_rp[row + 1] - b), o = (int32_t)(p - b);
+            const int32_t rank = from.order == 0 ? row_rank(o, L) : o;
+            pt = b + (to.order == 0 ? row_position(rank, L) : rank);
         }
+        const int64_t c = pt / to.T;
+        const int64_t t = pt - c * to.T;
+        const int64_t slot = chunk_slot(to, c);
+        dst[chunk_entry_index(slot, to.S, to.T, t)] = src[q];
+        if (t == 0) meta[slot] = make_int2(row >= 0 ? row : row_of(pt), (int32_t)c);
     }
 }
 

@@ -84,6 +84,7 @@ struct ChunkLayout {
     int64_t S;     // chunks (slots)
     int64_t mul;   // slot of chunk c: (mul * c + add) mod S, gcd(mul, S) = 1
     int64_t add;
+    int32_t order = 0;   // entries within a row: 0 affine order of their partners, 1 ascending partner id
 };
 
 __host__ __device__ inline int64_t chunk_slot(const ChunkLayout &L, int64_t c) {

@@ -35,12 +35,13 @@ def _row_position(q: int, L: int) -> int:
     return (a * q) % L
 
 
-def oriented_order(g) -> np.ndarray:
+def oriented_order(g, ascending: bool = False) -> np.ndarray:
     """Visiting order of the directed CSR edges by one Hogwild lane (built
     here from the documented rule, independently of the library): every
     undirected edge in the row of its higher-ranked endpoint (degree, then
     smaller id); a row's entries in ascending partner id, then stored at
-    _row_position; rows in vertex order; per entry (i, j) then (j, i)."""
+    _row_position (or left ascending: the row order SNAP_FLAG_ASCENDING_ROWS
+    selects); rows in vertex order; per entry (i, j) then (j, i)."""
     rp, ci = g.row_ptr, g.col_idx
     deg = np.diff(rp)
     order = []
@@ -54,7 +55,7 @@ def oriented_order(g) -> np.ndarray:
                 row.append((e, rev))
         placed = [None] * len(row)
         for q, pair in enumerate(row):
-            placed[_row_position(q, len(row))] = pair
+            placed[q if ascending else _row_position(q, len(row))] = pair
         for e, rev in placed:
             order += [e, rev]
     assert sorted(order) == list(range(g.nnz))

@@ -64,7 +64,7 @@ def _ctypes_of(decl):
 
 def test_binding_arguments_match_header(lib):
     decls = _declared_parameters()
-    assert len(decls["snap_layout_autotune"]) == 13 and len(decls["snap_layout_epochs"]) == 8
+    assert len(decls["snap_layout_autotune"]) == 14 and len(decls["snap_layout_epochs"]) == 8
     for name, params in decls.items():
         argtypes = getattr(lib, name).argtypes
         assert argtypes is not None, f"{name} has no argtypes in the binding"
@@ -143,7 +143,7 @@ def test_host_side_argument_errors(lib):
                 dict(sync_cap=-1.0), dict(block_threads=512), dict(max_inflight=1.5)):
         assert _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=snap.make_options(**bad))[0] == 1, bad
     o = snap.make_options()
-    o.flags = 6
+    o.flags = 8
     st, msg = _status(snap.snap_layout_create, g.row_ptr, g.col_idx, opts=o)
     assert st == 1 and "flags" in msg
 
@@ -157,7 +157,7 @@ def test_null_handle_errors(lib):
     assert lib.snap_layout_epochs(None, P(8), 0, 1, 3, ctypes.byref(sched), 1, None) == 1
     assert b"NULL" in lib.snap_last_error()
     assert lib.snap_layout_autotune(None, P(8), P(8), 3, ctypes.byref(sched), 1, 0.02, None, None, None, None,
-                                    None, None) == 1
+                                    None, None, None) == 1
     assert b"NULL" in lib.snap_last_error()
 
 

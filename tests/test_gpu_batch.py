@@ -132,7 +132,7 @@ def test_autotune_picks_a_bounded_configuration(cuda):
     sched = snap.linear_schedule(1.0, 10)
     scratch = torch.from_numpy(initial_positions(g.n, 1)).cuda()
     with snap.Layout(g.row_ptr, g.col_idx) as L:
-        seg, blk, ms, u, _ = snap.snap_layout_autotune(L.handle, scratch, 3, sched, 7)   # timing only
+        seg, blk, ms, u, _, _ = snap.snap_layout_autotune(L.handle, scratch, 3, sched, 7)   # timing only
         assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0 and np.isnan(u)
         pos = torch.from_numpy(initial_positions(g.n, 2)).cuda()
         before = L.objective(pos, 3)[2]
@@ -162,7 +162,7 @@ def test_autotune_quality_gate(cuda, mode):
         L.epochs(pos, 0, 10, 3, sched, 5)
         L.check()
         u_entry = L.objective(pos, 3, exact=False, pair_samples=1 << 24, seed=5 ^ 0x5bd1e9955bd1e995)[2]
-        seg, blk, ms, u, _ = L.autotune(init, scratch, 3, sched, 5, tolerance=0.02)
+        seg, blk, ms, u, _, _ = L.autotune(init, scratch, 3, sched, 5, tolerance=0.02)
         assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0
         # the gate compares against its own run of the entry configuration;
         # u_entry is another run of it (Hogwild runs differ by well under 1%)
@@ -173,7 +173,7 @@ def test_autotune_quality_gate(cuda, mode):
         again = L.objective(pos, 3, exact=False, pair_samples=1 << 24, seed=5 ^ 0x5bd1e9955bd1e995)[2]
         assert again == pytest.approx(u, rel=0.02)
     with snap.Layout(g.row_ptr, g.col_idx, opts=opts) as L:
-        seg0, blk0, _, u0, _ = L.autotune(init, scratch, 3, sched, 5, tolerance=0.0)
+        seg0, blk0, _, u0, _, _ = L.autotune(init, scratch, 3, sched, 5, tolerance=0.0)
         assert seg0 in (4, 8, 16, 32) and blk0 in (128, 256)
         assert np.isfinite(u0) and u0 <= u_entry * 1.01
 
@@ -192,7 +192,7 @@ def test_autotune_on_a_batch_with_a_captured_epoch_loop(cuda):
     pos = torch.empty_like(init)
     h = snap.snap_layout_create_batch(rp, ci, offs, snap.make_options(cuda_graph=True))
     try:
-        seg, blk, ms, u, _ = snap.snap_layout_autotune(h, scratch, 3, sched, 2, init, 0.02)
+        seg, blk, ms, u, _, _ = snap.snap_layout_autotune(h, scratch, 3, sched, 2, init, 0.02)
         assert seg in (4, 8, 16, 32) and blk in (128, 256) and ms > 0 and np.isfinite(u)
         pos.copy_(init)
         before = snap.snap_layout_objective(h, pos, 3, True)[2]

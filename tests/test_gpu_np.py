@@ -76,7 +76,7 @@ def test_autotune_gates_on_np_in_a_batch(cuda):
     scratch = torch.empty_like(init)
     h = snap.snap_layout_create_batch(rp, ci, offs, snap.make_options(keep_csr=True))
     try:
-        seg, blk, ms, u, npv = snap.snap_layout_autotune(h, scratch, 3, sched, 5, init, 0.02)
+        seg, blk, ms, u, npv, order = snap.snap_layout_autotune(h, scratch, 3, sched, 5, init, 0.02)
         assert np.isfinite(u) and 0.0 < npv <= 1.0
         print(f"autotune with NP gate: chunk {seg}, block {blk}, {ms:.3f} ms/epoch, U {u:.1f}, NP {npv:.4f}")
     finally:

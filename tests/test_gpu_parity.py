@@ -101,6 +101,25 @@ def test_single_lane_hogwild_is_algorithm1_in_oriented_order(cuda, mode, n, m, k
     assert err < SYNC_RTOL
 
 
+@pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
+@pytest.mark.parametrize("n,m,k", [(40, 120, 3), (300, 900, 4)])
+def test_single_lane_hogwild_with_ascending_rows(cuda, mode, n, m, k):
+    """The row order the autotuner may choose (entries of a row in ascending
+    partner id): one lane is Algorithm 1 in that order.  Also after the
+    handle's order was switched by a re-layout (autotune)."""
+    g = tiny_graph(n, m, seed=n)
+    Y0 = initial_positions(g.n, 4)
+    sched = snap.linear_schedule(eta0=0.5, total_epochs=4)
+    flags_opts = snap.make_options(mode=mode, segment_edges=4096)
+    flags_opts.flags |= snap.FLAG_ASCENDING_ROWS
+    got = gpu_layout(cuda, g, Y0, 2, k, sched, seed=21, opts=flags_opts)
+    ref = oracle.seq(g.row_ptr, g.col_idx, g.n, Y0, 2, k, schedule_dict(sched), seed=21,
+                     order=oriented_order(g, ascending=True))
+    err = parity_error(got, ref)
+    print(f"single-lane hogwild, ascending rows, n={n} k={k} mode={mode}: max rel err {err:.2e}")
+    assert err < SYNC_RTOL
+
+
 # --------------------------------------------------------------------------
 # Hogwild quality against the oracle (Algorithm 1, shuffled) over 5 seeds
 # --------------------------------------------------------------------------
