@@ -190,8 +190,7 @@ struct snap_layout {
     int4 *d_act_ent = nullptr;
     int2 *d_act_meta = nullptr;
     int64_t act_ent_bytes = 0, act_meta_bytes = 0;
-    bool act_narrow = false;              // entries carry their source (fewer than 2^32 directed edges)
-    int32_t *d_act_pieces = nullptr;      // chunks each vertex's oriented row spans (narrow lists)
+    int32_t *d_act_pieces = nullptr;      // chunks each vertex's oriented row spans
     int64_t act_pieces_bytes = 0;
     // batch of graphs (num_graphs > 1): graph of every vertex and per-graph table
     int32_t num_graphs = 1;
@@ -340,7 +339,7 @@ static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, 
         if (meta) cudaFreeAsync(meta, stream);
         return err;
     }
-    if (h->act_narrow) {
+    {
         // the per-vertex piece counts depend on the chunk size
         if (!h->d_act_pieces) {
             const int64_t pb = (int64_t)sizeof(int32_t) * (h->n > 0 ? h->n : 1);
@@ -377,7 +376,6 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
     const int32_t n = h->n;
     const int64_t nnz = h->nnz;
     h->act_nnz = nnz / 2;   // symmetric and loop-free: each undirected edge once
-    h->act_narrow = nnz < ((int64_t)1 << 32);   // 32-bit edge indices: the entry's spare word holds the source
     if (h->act_seg_len == 0) {
         // Default chunk: 4 entries.  A lane applies a chunk's steps of one
         // source back to back; long bursts of one source's steps move the
@@ -418,7 +416,7 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
              "orientation flags kernel");
         step(exclusive_scan_i32(temp, &temp_bytes, flags, pos, nnz + 1, stream), "orientation scan");
         step(launch_orient_scatter(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, pos,
-                                   h->d_act_ent, h->act_narrow ? 1 : 0, stream), "orientation scatter kernel");
+                                   h->d_act_ent, stream), "orientation scatter kernel");
         step(launch_orient_rowptr(h->d_row_ptr, pos, n, h->d_act_row_ptr, stream), "orientation offsets kernel");
     }
     int64_t total = -1;
@@ -878,7 +876,6 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
             a.graphs = h->num_graphs > 1 ? h->d_graphs : nullptr;
             a.alias = h->d_alias;
             a.energy = energy ? energy + ep : nullptr;
-            a.narrow = h->act_narrow ? 1 : 0;
             a.pieces = h->d_act_pieces;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
             const int g = neg_samples < 4 ? neg_samples : 4;
@@ -1582,7 +1579,7 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
         jd.nnz = h->act_nnz;
         jd.seg_len = h->act_seg_len;
         jd.alias = h->d_alias;
-        jd.narrow = h->act_narrow ? 1 : 0;
+        jd.pieces = h->d_act_pieces;
         jd.seg_prefix = total;
         jd.seed = seeds[q];
         jd.n = h->n;

@@ -165,14 +165,9 @@ __device__ __forceinline__ void later_negatives(const OrientedArgs &a, const Gra
 }
 
 // The CSR indices of an entry's two directed copies (i, j) and (j, i).
-__device__ __forceinline__ void entry_edges(const OrientedArgs &a, int4 ent, int64_t &e1, int64_t &e2) {
-    if (a.narrow) {
-        e1 = (int64_t)(uint32_t)ent.y;
-        e2 = (int64_t)(uint32_t)ent.z;
-    } else {
-        e1 = (int64_t)(uint32_t)ent.y | ((int64_t)((uint32_t)ent.w & 0xFFFFu) << 32);
-        e2 = (int64_t)(uint32_t)ent.z | ((int64_t)((uint32_t)ent.w >> 16) << 32);
-    }
+__device__ __forceinline__ void entry_edges(int4 ent, int64_t &e1, int64_t &e2) {
+    e1 = (int64_t)(uint32_t)ent.y;
+    e2 = (int64_t)(uint32_t)ent.z;
 }
 
 template <bool RED, int G, bool W, bool E>
@@ -292,19 +287,13 @@ __device__ __forceinline__ int row_pieces(int64_t row_begin, int64_t row_end, in
 
 // One chunk: the source y_i of the current row is held in registers and
 // written back when the walk leaves the row.
-// SNAP_ENT_PREFETCH (build switch): each entry of the chunk is loaded while
-// the previous one is processed (the first together with the slot
-// descriptor), so the stream's latency overlaps the gathers and updates.
-#ifndef SNAP_ENT_PREFETCH
-#define SNAP_ENT_PREFETCH 0
-#endif
+// Each entry of the chunk is loaded while the previous one is processed (the
+// first together with the slot descriptor).
 template <bool RED, int G, bool MULTI, bool W, bool E>
 __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t slot, uint32_t &flags, float &en) {
     const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
     const int64_t step = chunk_group_width(slot, a.num_segs);
-#if SNAP_ENT_PREFETCH
     int4 ent_next = load_entry(ep);   // every stored chunk has at least one entry
-#endif
     const int2 mt = __ldg(a.meta + slot);   // {row of the first entry, chunk}
     int32_t row = mt.x;
     int64_t p = (int64_t)mt.y * a.seg_len;
@@ -327,16 +316,11 @@ __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t sl
             yi = load_pos(a.pos + row);
             yi0 = yi;
         }
-#if SNAP_ENT_PREFETCH
-        const int4 ent = ent_next;   // {j, indices of (i, j) and (j, i), source or their high bits}
+        const int4 ent = ent_next;   // {j, indices of (i, j) and (j, i), i}
         if (p + 1 < p1) ent_next = load_entry(ep + step);
         if (!c.active) continue;
-#else
-        if (!c.active) continue;
-        const int4 ent = load_entry(ep);   // {j, indices of (i, j) and (j, i), source or their high bits}
-#endif
         int64_t e1, e2;
-        entry_edges(a, ent, e1, e2);
+        entry_edges(ent, e1, e2);
         oriented_entry<RED, G, W, E>(a, c, row, ent.x, e1, e2, yi, en);
     }
     if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
@@ -344,18 +328,13 @@ __device__ __forceinline__ void oriented_chunk(const OrientedArgs &a, int64_t sl
 }
 
 // ---------------------------------------------------------------------------
-// Software-pipelined chunk walk (build switch SNAP_PIPE; uniform negatives,
-// k <= 4).  The next entry's random words are drawn and its k + k + 1
-// gathers issued before the current entry's updates, so a lane keeps two
-// entries' loads in flight.  Values gathered early for a vertex that the
-// current entry then updates are replaced by the lane's own latest value
-// (forwarding), so one lane alone still applies Algorithm 1's updates in
-// its order exactly; across lanes the early gathers are as racy as any.
+// Pipelining helpers of the direct walk below: an entry is staged (its
+// random words drawn, its k + k + 1 gathers issued) one entry ahead of its
+// updates.  Values gathered early for a vertex that the entry in between
+// then writes are replaced by what this lane's write leaves in memory
+// (forwarding), so one lane alone still applies Algorithm 1's updates in its
+// order exactly; across lanes the early gathers are as racy as any.
 // ---------------------------------------------------------------------------
-#ifndef SNAP_PIPE
-#define SNAP_PIPE 0
-#endif
-
 struct StagedEntry {
     int32_t j;
     int32_t s1[4], s2[4];   // negatives of (i, j) (source i) and of (j, i) (source j)
@@ -367,7 +346,7 @@ __device__ __forceinline__ void stage_entry(const OrientedArgs &a, const GraphCt
                                             StagedEntry &st) {
     st.j = ent.x;
     int64_t e1, e2;
-    entry_edges(a, ent, e1, e2);
+    entry_edges(ent, e1, e2);
     if (G > 0) {
         const uint4 w1 = words_in(c, e1, 0u);
         const uint4 w2 = words_in(c, e2, 0u);
@@ -465,89 +444,26 @@ __device__ __forceinline__ float2 written_source(const OrientedArgs &a, float2 y
                        __fadd_rn(yi0.y, __fmul_rn(__fsub_rn(yi.y, yi0.y), inv)));
 }
 
-template <bool RED, int G, bool MULTI, bool E>
-__device__ __forceinline__ void oriented_chunk_pipe(const OrientedArgs &a, int64_t slot, uint32_t &flags, float &en) {
-    const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
-    const int64_t step = chunk_group_width(slot, a.num_segs);
-    int4 ent_next = load_entry(ep);   // every stored chunk has at least one entry
-    const int2 mt = __ldg(a.meta + slot);   // {row of the first entry, chunk}
-    int32_t row = mt.x;
-    int64_t p = (int64_t)mt.y * a.seg_len;
-    const int64_t p1 = p + a.seg_len < a.nnz ? p + a.seg_len : a.nnz;
-    int64_t row_begin = RED ? __ldg(a.row_ptr + row) : 0;
-    int64_t row_end = __ldg(a.row_ptr + row + 1);
-    GraphCtx c = graph_ctx<MULTI>(a, row);
-    float2 yi = load_pos(a.pos + row);
-    float2 yi0 = yi;
-    StagedEntry cur, nxt;
-    if (c.active) stage_entry<G>(a, c, row, ent_next, cur);
-    if (p + 1 < p1) ent_next = load_entry(ep + step);
-    for (; p < p1; ++p) {
-        // the next entry's row, graph and gathers, issued before this entry's updates
-        const bool more = p + 1 < p1;
-        int32_t row_n = row;
-        int64_t rb_n = row_begin, re_n = row_end;
-        GraphCtx c_n = c;
-        float2 yi_n = yi;
-        if (more) {
-            if (p + 1 >= re_n) {
-                do {
-                    ++row_n;
-                    rb_n = re_n;
-                    re_n = __ldg(a.row_ptr + row_n + 1);
-                } while (re_n <= p + 1);
-                if (MULTI) c_n = graph_ctx<MULTI>(a, row_n);
-                yi_n = load_pos(a.pos + row_n);
-            }
-            if (c_n.active) stage_entry<G>(a, c_n, row_n, ent_next, nxt);
-            if (p + 2 < p1) ent_next = load_entry(ep + 2 * step);
-            ep += step;
-        }
-        if (c.active) finish_entry<RED, G, E>(a, c.eta, row, cur, yi, en);
-        if (!more) break;
-        if (row_n != row) {
-            const int pieces = RED ? row_pieces(row_begin, row_end, a.seg_len) : 1;
-            float2 mem = yi;
-            if (c.active) {
-                write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
-                mem = written_source<RED>(a, yi, yi0, pieces);
-                yi_n = forwarded<G>(row_n, yi_n, cur, row, mem);
-                if (c_n.active) forward_into<G>(nxt, cur, row, mem);
-            }
-            row = row_n;
-            row_begin = rb_n;
-            row_end = re_n;
-            c = c_n;
-            yi = yi_n;
-            yi0 = yi;
-        } else if (c.active) {
-            forward_into<G>(nxt, cur, row, yi);
-        }
-        cur = nxt;
-    }
-    if (c.active) write_oriented_source<RED>(a, row, yi, yi0, RED ? row_pieces(row_begin, row_end, a.seg_len) : 1,
-                                             flags);
-}
-
 // ---------------------------------------------------------------------------
-// Direct chunk walk (the default for single graphs with uniform negatives,
-// k <= 4 and narrow entries).  Every entry names its source, so a lane needs
-// no row offsets: the first entry of a chunk gives the row, and a change of
-// source in a later entry is a row change.  The walk is pipelined as
-// oriented_chunk_pipe (the next entry's words drawn and its gathers issued
-// before the current entry's updates, with forwarding of the lane's own
-// writes), and the kernel loop below also loads the lane's next chunk's first
-// entry and slot descriptor before it walks the current one, so the stream's
-// latency is hidden too.  HOGWILD_RED reads the row's piece count (the chunks
-// the row spans) when the row starts, for the write-back's scaling.
-// SNAP_DIRECT = 0 (build switch) keeps the row-offset walks for every case.
+// Direct chunk walk (the default with uniform negatives and k <= 4, for
+// single graphs, batches and multi-handle epochs).  Every entry names its
+// source, so a lane needs no row offsets: the first entry of a chunk gives
+// the row, and a change of source in a later entry is a row change (in a
+// batch, the graph is looked up then).  The next entry's words are drawn and
+// its gathers issued before the current entry's updates, with forwarding of
+// the lane's own writes, and the slot loop below also loads the lane's next
+// chunk's first entry and slot descriptor before it walks the current one,
+// so the stream's latency is hidden too.  HOGWILD_RED reads the row's piece
+// count (the chunks the row spans) when the row starts, for the write-back's
+// scaling.  SNAP_DIRECT = 0 (build switch) keeps the row-offset walk for
+// every case.
 // ---------------------------------------------------------------------------
 #ifndef SNAP_DIRECT
 #define SNAP_DIRECT 1
 #endif
 
-template <bool RED, int G>
-__device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, const GraphCtx &c, int64_t slot,
+template <bool RED, int G, bool MULTI>
+__device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, const GraphCtx &c0, int64_t slot,
                                                       int4 ent0, int2 mt, uint32_t &flags) {
     const int64_t step = chunk_group_width(slot, a.num_segs);
     const int4 *ep = a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0);
@@ -555,52 +471,60 @@ __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, con
     const int32_t len = (int32_t)(a.nnz - first < (int64_t)a.seg_len ? a.nnz - first : (int64_t)a.seg_len);
     float en = 0.0f;
     int32_t row = ent0.w;
+    GraphCtx c = MULTI ? graph_ctx<true>(a, row) : c0;   // a batch: the source's graph
     float2 yi = load_pos(a.pos + row);
     int32_t pieces = RED ? __ldg(a.pieces + row) : 1;
     StagedEntry cur, nxt;
-    stage_entry<G>(a, c, row, ent0, cur);
+    if (c.active) stage_entry<G>(a, c, row, ent0, cur);
     int4 ent_next = len > 1 ? load_entry(ep + step) : ent0;
     float2 yi0 = yi;
     for (int32_t q = 0; q < len; ++q) {
         const bool more = q + 1 < len;
         int32_t row_n = row, pieces_n = pieces;
         float2 yi_n = yi;
+        GraphCtx c_n = c;
         if (more) {
             row_n = ent_next.w;
             if (row_n != row) {
                 yi_n = load_pos(a.pos + row_n);
                 if (RED) pieces_n = __ldg(a.pieces + row_n);
+                if (MULTI) c_n = graph_ctx<true>(a, row_n);
             }
-            stage_entry<G>(a, c, row_n, ent_next, nxt);
+            if (c_n.active) stage_entry<G>(a, c_n, row_n, ent_next, nxt);
             if (q + 2 < len) ent_next = load_entry(ep + (int64_t)(q + 2) * step);
         }
-        finish_entry<RED, G, false>(a, c.eta, row, cur, yi, en);
+        if (c.active) finish_entry<RED, G, false>(a, c.eta, row, cur, yi, en);
         if (!more) break;
         if (row_n != row) {
-            write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
-            const float2 mem = written_source<RED>(a, yi, yi0, pieces);
-            yi_n = forwarded<G>(row_n, yi_n, cur, row, mem);
-            forward_into<G>(nxt, cur, row, mem);
+            if (c.active) {
+                write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
+                const float2 mem = written_source<RED>(a, yi, yi0, pieces);
+                if (c_n.active) {
+                    yi_n = forwarded<G>(row_n, yi_n, cur, row, mem);
+                    forward_into<G>(nxt, cur, row, mem);
+                }
+            }
             row = row_n;
+            c = c_n;
             yi = yi_n;
             yi0 = yi;
             pieces = pieces_n;
-        } else {
+        } else if (c.active) {
             forward_into<G>(nxt, cur, row, yi);
         }
         cur = nxt;
     }
-    write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
+    if (c.active) write_oriented_source<RED>(a, row, yi, yi0, pieces, flags);
 }
 
 // The lanes' slot loop of the direct walk: the next chunk's first entry and
 // descriptor are in flight while the current chunk is walked.
-template <bool RED, int G>
+template <bool RED, int G, bool MULTI>
 __device__ __forceinline__ void direct_slots(const OrientedArgs &a, uint32_t &flags) {
     const int64_t groups = (a.num_segs + 31) >> 5;
     const int64_t limit = groups << 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const GraphCtx c = graph_ctx<false>(a, 0);
+    const GraphCtx c = graph_ctx<false>(a, 0);   // single graph (a batch looks its graph up per row)
     int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t ws = w < limit ? slot_of(w, groups, a.perm_mul, a.perm_add) : a.num_segs;
     int4 ent0 = make_int4(0, 0, 0, 0);
@@ -618,7 +542,7 @@ __device__ __forceinline__ void direct_slots(const OrientedArgs &a, uint32_t &fl
             ent2 = load_entry(a.ent + chunk_entry_index(ws2, a.num_segs, a.seg_len, 0));
             mt2 = __ldg(a.meta + ws2);
         }
-        if (ws < a.num_segs) oriented_chunk_direct<RED, G>(a, c, ws, ent0, mt, flags);
+        if (ws < a.num_segs) oriented_chunk_direct<RED, G, MULTI>(a, c, ws, ent0, mt, flags);
         w = w2;
         ws = ws2;
         ent0 = ent2;
@@ -634,8 +558,8 @@ template <bool RED, int G, bool MULTI, bool W, bool E>
 __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_kernel(const OrientedArgs a) {
     uint32_t flags = 0;
     double energy = 0.0;
-    if (SNAP_DIRECT && !MULTI && !W && !E && a.narrow && a.k <= 4 && (!RED || a.pieces)) {
-        direct_slots<RED, G>(a, flags);
+    if (SNAP_DIRECT && !W && !E && a.k <= 4 && (!RED || a.pieces)) {
+        direct_slots<RED, G, MULTI>(a, flags);
         if (flags) atomicOr(a.status, flags);
         return;
     }
@@ -644,12 +568,7 @@ __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (groups << 5); w += stride) {
         const int64_t ws = slot_of(w, groups, a.perm_mul, a.perm_add);
         float en = 0.0f;
-        if (ws < a.num_segs) {
-            if (SNAP_PIPE && !W && a.k <= 4)
-                oriented_chunk_pipe<RED, G, MULTI, E>(a, ws, flags, en);
-            else
-                oriented_chunk<RED, G, MULTI, W, E>(a, ws, flags, en);
-        }
+        if (ws < a.num_segs) oriented_chunk<RED, G, MULTI, W, E>(a, ws, flags, en);
         if (E) energy += (double)en;
     }
     if (flags) atomicOr(a.status, flags);
@@ -703,13 +622,18 @@ __global__ void __launch_bounds__(256, SNAP_MULTI_MIN_BLOCKS) multi_epoch_kernel
         a.inflight_share = m.inflight_share;
         a.alias = jd.alias;
         a.energy = nullptr;
-        a.narrow = jd.narrow;
-        a.pieces = nullptr;
+        a.pieces = jd.pieces;
         float en = 0.0f;
-        if (WEIGHTED && G > 0 && a.alias)
-            oriented_chunk<RED, G, false, true, false>(a, ws - jd.seg_prefix, flags, en);
-        else
-            oriented_chunk<RED, G, false, false, false>(a, ws - jd.seg_prefix, flags, en);
+        const int64_t slot = ws - jd.seg_prefix;
+        if (WEIGHTED && G > 0 && a.alias) {
+            oriented_chunk<RED, G, false, true, false>(a, slot, flags, en);
+        } else if (SNAP_DIRECT && a.k <= 4 && (!RED || a.pieces)) {
+            const int4 ent0 = load_entry(a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0));
+            const int2 mt = __ldg(a.meta + slot);
+            oriented_chunk_direct<RED, G, false>(a, graph_ctx<false>(a, 0), slot, ent0, mt, flags);
+        } else {
+            oriented_chunk<RED, G, false, false, false>(a, slot, flags, en);
+        }
     }
     if (flags) atomicOr(m.status, flags);
 }

@@ -124,15 +124,11 @@ __global__ void orient_flags_kernel(const int64_t *__restrict__ row_ptr, const i
     if (blockIdx.x == 0 && threadIdx.x == 0) flags[nnz] = 0;
 }
 
-// Entry of an oriented edge {i, j}.  Narrow lists (fewer than 2^32 directed
-// edges): {j, index of (i, j), index of (j, i), i}, so an entry names its
-// own source.  Wide lists: {j, low 32 bits of the two indices, their bits
-// 32..47 packed in .w} (up to 2^48 directed edges; the source is found from
-// the row offsets).
-__device__ __forceinline__ int4 make_entry(int32_t i, int32_t j, int64_t fwd, int64_t rev, bool narrow) {
-    if (narrow) return make_int4(j, (int32_t)(uint32_t)fwd, (int32_t)(uint32_t)rev, i);
-    const uint32_t hi = (uint32_t)((fwd >> 32) & 0xFFFF) | ((uint32_t)((rev >> 32) & 0xFFFF) << 16);
-    return make_int4(j, (int32_t)(uint32_t)fwd, (int32_t)(uint32_t)rev, (int32_t)hi);
+// Entry of an oriented edge {i, j}: {j, index of (i, j), index of (j, i), i}
+// -- the CSR indices of both directed copies (a handle holds fewer than 2^32
+// directed edges) and the source, so an entry names its own row.
+__device__ __forceinline__ int4 make_entry(int32_t i, int32_t j, int64_t fwd, int64_t rev) {
+    return make_int4(j, (int32_t)(uint32_t)fwd, (int32_t)(uint32_t)rev, i);
 }
 
 // Order of the entries inside an oriented row of length L: the entry of
@@ -186,7 +182,7 @@ __device__ __forceinline__ int32_t row_rank(int32_t o, int32_t L) {
 __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                       const int32_t *__restrict__ seg_row, const int32_t *__restrict__ deg,
                                       int64_t nnz, int32_t seg_len, const int32_t *__restrict__ pos,
-                                      int4 *__restrict__ ent, int narrow) {
+                                      int4 *__restrict__ ent) {
     for_each_edge(row_ptr, col_idx, seg_row, nnz, seg_len, [&](int64_t e, int32_t i, int32_t j) {
         if (!ranks_higher(deg[i], deg[j], i, j)) return;
         const int32_t start = pos[row_ptr[i]];
@@ -200,7 +196,7 @@ __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const
             else
                 hi = mid;
         }
-        ent[p] = make_entry(i, j, e, lo, narrow != 0);
+        ent[p] = make_entry(i, j, e, lo);
     });
 }
 
@@ -530,10 +526,10 @@ cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in
 
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                   const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  int narrow, cudaStream_t s) {
+                                  cudaStream_t s) {
     const int64_t segs = (nnz + seg_len - 1) / seg_len;
     orient_scatter_kernel<<<grid_for(segs, 256), 256, 0, s>>>(row_ptr, col_idx, seg_row, deg, nnz, seg_len, pos,
-                                                             ent, narrow);
+                                                             ent);
     return cudaGetLastError();
 }
 

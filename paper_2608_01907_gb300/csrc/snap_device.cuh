@@ -105,55 +105,16 @@ __device__ __forceinline__ float2 repulsion_on_i(float dx, float dy) {
     return make_float2(cr * dx, cr * dy);
 }
 
-// Build variants of the position and entry accesses (compile-time switches,
-// 0 = the plain CUDA intrinsics):
-//   SNAP_PTX_RED  displacement adds as one vector red.global.add.v2.f32
-//   SNAP_L2_HINT  position loads and adds carry an L2 evict_last policy, the
-//                 streamed entries an L2 evict_first policy and no L1 allocation
-#ifndef SNAP_PTX_RED
-#define SNAP_PTX_RED 0
-#endif
-#ifndef SNAP_L2_HINT
-#define SNAP_L2_HINT 0
-#endif
-
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
 // Position accesses that must see other SMs' writes: cached in L2 only.
-__device__ __forceinline__ float2 load_pos(const float2 *p) {
-#if SNAP_L2_HINT
-    float2 v;
-    asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-                 : "=f"(v.x), "=f"(v.y)
-                 : "l"(p), "l"(policy_evict_last()));
-    return v;
-#else
-    return __ldcg(p);
-#endif
-}
+// (Measured on GB300 against these intrinsics, with no gain on the R-MAT
+// epoch: an explicit vector red.global.add.v2.f32, L2 evict-last / evict-first
+// cache policies on positions and entries.)
+__device__ __forceinline__ float2 load_pos(const float2 *p) { return __ldcg(p); }
 
-// Adds d to a position (relaxed, device scope, no return value).
-__device__ __forceinline__ void add_pos(float2 *p, float2 d) {
-#if SNAP_L2_HINT
-    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(d.x),
-                 "f"(d.y), "l"(policy_evict_last())
-                 : "memory");
-#elif SNAP_PTX_RED
-    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(d.x), "f"(d.y) : "memory");
-#else
-    atomicAdd(p, d);
-#endif
-}
+// Adds d to a position (relaxed, device scope, no return value: a vector
+// reduction in L2).
+__device__ __forceinline__ void add_pos(float2 *p, float2 d) { atomicAdd(p, d); }
+
 // A position written as one 64-bit atomic exchange (racy, last writer wins).
 __device__ __forceinline__ void exchange_pos(float2 *p, float2 v) {
     unsigned long long bits;
@@ -166,21 +127,9 @@ __device__ __forceinline__ int4 load_cols4(const int32_t *p) {
     return __ldcs(reinterpret_cast<const int4 *>(p));
 }
 
-// One oriented entry {j, low 32 bits of the indices of (i, j) and (j, i),
-// their bits 32..47}.
-// Read through L1: the 32 lanes of a warp walk one compact run of entries
-// over several iterations, so a line fetched for one lane serves others.
-__device__ __forceinline__ int4 load_entry(const int4 *p) {
-#if SNAP_L2_HINT
-    int4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p), "l"(policy_evict_first()));
-    return v;
-#else
-    return __ldg(p);
-#endif
-}
+// One oriented entry {j, index of (i, j), index of (j, i), i}.  Read through
+// L1: the 32 lanes of a warp read one 512-byte run of entries per step.
+__device__ __forceinline__ int4 load_entry(const int4 *p) { return __ldg(p); }
 
 // int64 fixed point (2^-32) of one force component, clamped to +-2^20.
 __device__ __forceinline__ long long to_fixed(float v, uint32_t &flags) {

@@ -103,7 +103,7 @@ __host__ __device__ inline int64_t chunk_entry_index(int64_t slot, int64_t S, in
 
 struct OrientedArgs {
     const int64_t *row_ptr;   // n + 1 row offsets of the oriented list (row-major positions)
-    const int4 *ent;          // entries in the stored (slot-interleaved) order
+    const int4 *ent;          // entries {j, index of (i, j), index of (j, i), i}, stored slot-interleaved
     const int2 *meta;         // per slot: {row of the chunk's first entry, chunk id}
     float2 *pos;
     int64_t num_segs;         // slots S
@@ -122,8 +122,7 @@ struct OrientedArgs {
     float inflight_share;        // lanes in flight / slots (share of the chunks running at once)
     const uint2 *alias;          // weighted negatives (alias table, graph-local ids); null: uniform
     double *energy;              // actual energy of the epoch is added here (null: not computed)
-    int32_t narrow;              // entries {j, (i, j), (j, i), i}: 32-bit edge indices, the source in .w
-    const int32_t *pieces;       // narrow lists: chunks each vertex's oriented row spans (HOGWILD_RED)
+    const int32_t *pieces;       // chunks each vertex's oriented row spans (HOGWILD_RED's write-back)
 };
 
 // Dispatches on a.alias (weighted negatives, epoch_weighted.cu) and a.energy
@@ -151,7 +150,7 @@ struct JobDesc {
     float eta;
     int32_t seg_len;
     const uint2 *alias;     // the job's alias table, or null (uniform)
-    int32_t narrow;         // the job's entry format (OrientedArgs::narrow)
+    const int32_t *pieces;  // the job's per-vertex piece counts (OrientedArgs::pieces)
 };
 
 struct MultiArgs {
@@ -195,7 +194,7 @@ cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in
                                cudaStream_t s);
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                   const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  int narrow, cudaStream_t s);
+                                  cudaStream_t s);
 // pieces[v] = chunks of T entries that v's oriented row spans.
 cudaError_t launch_row_pieces(const int64_t *act_rp, int32_t n, int32_t T, int32_t *pieces, cudaStream_t s);
 cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,
