@@ -416,7 +416,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "s_per_layout_extrapolated": per_layout,
-            "config": workload_config(args, n, int(row_ptr[-1]), int((np.diff(row_ptr) == 0).sum())),
+            "config": dict(workload_config(args, n, int(row_ptr[-1]), int((np.diff(row_ptr) == 0).sum())),
+                           parallelism=f"replicas x{world}"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"each step: 1 epoch limited to {done} of {int(row_ptr[-1])} directed "
                                        f"edges, FP64 Algorithm 1, "
