@@ -806,7 +806,7 @@ def serve_result(args, local_rank, seconds):
                        "graph_pool": "48 graphs: R-MAT / 8-community planted partition, |E| log-uniform 1k-2M",
                        "mode": "hogwild_red",
                        "admission": "peak preparation bytes within the budget (half the free HBM at start) and "
-                                    "within the driver-reported free memory; reservation = handle bytes + positions",
+                                    "within the free device memory cudaMemGetInfo reports; reservation = handle bytes + positions",
                        "l2": "not flushed: a job's entries (<= 32 MB) and positions may stay in L2 across its "
                              "epochs, as they would in any server"},
             "continuous_batching": srv, "one_job_at_a_time": seq,

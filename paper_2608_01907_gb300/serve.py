@@ -4,8 +4,8 @@ Jobs (a graph, initial positions, a seed) arrive at any time.  Each tick of
 the server:
   1. admits waiting jobs, first come first served, while a slot is free and
      the job's peak device memory during preparation fits both the server's
-     HBM budget and the device's free memory as the driver reports it
-     (cudaMemGetInfo, read once per tick); the graph is copied to the device
+     HBM budget and the free device memory (cudaMemGetInfo, read once per
+     tick); the graph is copied to the device
      and prepared (snap_layout_create), and the job's reservation is then
      cut to what its handle really holds (snap_layout_device_bytes) plus its
      positions;
