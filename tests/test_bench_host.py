@@ -46,3 +46,34 @@ def test_replica_throughput_without_a_process_group():
     import bench
     ups, ms = bench.replica_throughput(250.0, 1e9)
     assert ms == 250.0 and ups == pytest.approx(4e9)
+
+
+def test_rooflines_follow_their_definitions():
+    """HBM term: 4 B per directed edge + 8 B per vertex; L2 term: 64 (k+1) B per
+    directed edge against the streaming-read probe; operation terms: (k+1)
+    loads and (k+1) atomic adds per directed edge against the probes; the
+    binding roofline is the term with the larger time."""
+    import bench
+    nnz, n, k, ms = 68_000_000, 4_194_304, 3, 3.5
+    probes = {"l2_read_bytes_per_s": 14e12, "random_loads_per_s": 300e9, "random_atomic_adds_per_s": 200e9,
+              "random_load_atomic_pairs_per_s": 80e9}
+    r = bench.rooflines(nnz, n, k, ms, probes, 6689.1, "measured", 663e6, "kernel")
+    hbm_bytes = 4 * nnz + 8 * (n + 1)
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == hbm_bytes
+    assert abs(r["hbm"]["frac"] - hbm_bytes / (ms / 1e3) / 1e9 / 6689.1) < 1e-12
+    assert abs(r["hbm"]["traffic_over_algorithmic"] - 663e6 / hbm_bytes) < 1e-12
+    l2_bytes = 64 * (k + 1) * nnz
+    assert r["l2"]["algorithmic_bytes_per_launch"] == l2_bytes
+    assert abs(r["l2"]["frac"] - l2_bytes / (ms / 1e3) / 14e12) < 1e-12
+    ops = (k + 1) * nnz
+    assert abs(r["ops"]["bound_ms"] - 1e3 * max(ops / 300e9, ops / 200e9)) < 1e-9
+    assert r["ops"]["binding"] == "atomic adds"
+    assert abs(r["ops"]["mixed_frac"] - ops / 80e9 / (ms / 1e3)) < 1e-12
+    assert r["binding"] is r["l2"]        # 17.4 GB at 14 TB/s outlasts 0.3 GB at 6.7 TB/s
+    # without probes only the HBM term is reported, and it binds
+    r = bench.rooflines(nnz, n, k, ms, None, 6689.1, "measured", None, "kernel")
+    assert r["l2"] is None and r["ops"] is None and r["binding"] is r["hbm"]
+    # the synchronous mode writes two 8-byte integer atomics per update
+    r = bench.rooflines(nnz, n, k, ms, probes, 6689.1, "measured", None, "kernel", sync=True)
+    assert r["l2"]["algorithmic_bytes_per_launch"] == 96 * (k + 1) * nnz
+    assert r["ops"]["atomic_adds_per_launch"] == 2 * ops and "mixed_frac" not in r["ops"]
