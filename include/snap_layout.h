@@ -147,7 +147,7 @@ void snap_options_default(snap_options *opts);
  * snap_layout_create -- validate a graph and make it resident on the device.
  *
  * Paper: the method needs only the directed edge list and the positions
- * (Section 3.3, "requires only two data structures"); the edge list is a CSR
+ * (Section 3.3: nothing but the edges and the positions); the edge list is a CSR
  * here, each undirected edge stored as (i, j) and (j, i).
  *
  *   row_ptr   host, n+1 int64; row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz < 2^32
@@ -250,7 +250,7 @@ snap_status snap_layout_sync_chunks(snap_layout_t h, float *positions, int32_t e
 
 /*
  * snap_layout_epochs_energy -- snap_layout_epochs that also reports the
- * "actual energy" of every epoch (Section 3.3, compared there with the
+ * actual energy of every epoch (Section 3.3, compared there with the
  * effective energy of Eq. 4 evaluated after each epoch): half the sum, over
  * the directed steps of the epoch, of U^a of the step's pair and U^r of each
  * drawn pair, each evaluated on the positions the update used (frozen

@@ -293,7 +293,8 @@ static uint64_t weight_total(const uint64_t *q, int32_t n)
     return Q;
 }
 
-/* Step size of epoch t (paper: "decaying over epochs", updated once per epoch). */
+/* Step size of epoch t (the paper: it decays with the epochs and changes once
+ * per epoch). */
 double oracle_step_size(int32_t kind, double eta0, double eta_min, int32_t total_epochs, int32_t t)
 {
     if (kind == 1)
@@ -375,7 +376,7 @@ static int32_t *row_of_edges(const int64_t *row_ptr, int32_t n)
 /* edges of the shuffled order are visited in each epoch (a timing sample). */
 /* actual_energy (nullable, one value per epoch): half the sum of U^a over  */
 /* the visited directed edges plus U^r over the drawn pairs, each taken at  */
-/* the moment of its update (Section 3.3, "actual energy").                 */
+/* the moment of its update (Section 3.3's actual energy).                  */
 /* Returns 0, or -1 on allocation failure.                                  */
 /* ------------------------------------------------------------------------ */
 int oracle_seq(const int64_t *row_ptr, const int32_t *col_idx, int32_t n, double *Y,
