@@ -339,14 +339,20 @@ struct StagedEntry {
     int32_t j;
     int32_t s1[4], s2[4];   // negatives of (i, j) (source i) and of (j, i) (source j)
     float2 yj, v1[4], v2[4];
+    int64_t e1, e2;         // the indices of (i, j) and (j, i) (the words of later negatives)
 };
 
-template <int G>
+// LATER (k > 4): the first four negatives of each direction are drawn here,
+// but only those of (i, j) are gathered; the rest are gathered when they are
+// applied (finish_entry), after this lane's earlier updates.
+template <int G, bool LATER = false>
 __device__ __forceinline__ void stage_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, int4 ent,
                                             StagedEntry &st) {
     st.j = ent.x;
     int64_t e1, e2;
     entry_edges(ent, e1, e2);
+    st.e1 = e1;
+    st.e2 = e2;
     if (G > 0) {
         const uint4 w1 = words_in(c, e1, 0u);
         const uint4 w2 = words_in(c, e2, 0u);
@@ -361,15 +367,58 @@ __device__ __forceinline__ void stage_entry(const OrientedArgs &a, const GraphCt
     st.yj = load_pos(a.pos + st.j);
 #pragma unroll
     for (int m = 0; m < G; ++m) st.v1[m] = load_pos(a.pos + st.s1[m]);
+    if (!LATER) {
 #pragma unroll
-    for (int m = 0; m < G; ++m) st.v2[m] = load_pos(a.pos + st.s2[m]);
+        for (int m = 0; m < G; ++m) st.v2[m] = load_pos(a.pos + st.s2[m]);
+    }
+}
+
+// Bits of the staged next entry (and the next row's source) that vertex x
+// matches: 1 = its partner, 2..16 = its first negatives of (i, j), 32 = the
+// next row's source.
+__device__ __forceinline__ uint32_t staged_match(const StagedEntry &nxt, int32_t row_n, int32_t x) {
+    uint32_t b = nxt.j == x ? 1u : 0u;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (nxt.s1[m] == x) b |= 2u << m;
+    if (row_n == x) b |= 32u;
+    return b;
+}
+
+// Negatives 4, 5, ... of a directed step (k > 4): gathered in groups of four
+// after this lane's earlier updates, applied, and every vertex they write
+// that the staged next entry already gathered is marked in `stale`.
+template <bool RED, bool E>
+__device__ __forceinline__ void later_direct(const OrientedArgs &a, const GraphCtx &c, int64_t ekey, int32_t src,
+                                             float2 &ysrc, int32_t other, float2 &yoth, const StagedEntry &nxt,
+                                             int32_t row_n, bool track, uint32_t &stale, float &en) {
+    for (int g = 1; g * 4 < a.k; ++g) {
+        const int nm = a.k - 4 * g < 4 ? a.k - 4 * g : 4;
+        const uint4 w = words_in(c, ekey, (uint32_t)g);
+        const int32_t s[4] = {negative_in(c, w.x, src), negative_in(c, w.y, src), negative_in(c, w.z, src),
+                              negative_in(c, w.w, src)};
+        float2 v[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (m < nm) v[m] = load_pos(a.pos + s[m]);
+        negative_group<RED, E>(a.pos, c.eta, s, v, nm, ysrc, other, yoth, en);
+        if (track) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (m < nm && s[m] != other) stale |= staged_match(nxt, row_n, s[m]);
+        }
+    }
 }
 
 // Both directed steps of a staged entry (the arithmetic of oriented_entry);
-// on return st.yj, st.v1 and st.v2 hold the values this lane wrote.
-template <bool RED, int G, bool E>
-__device__ __forceinline__ void finish_entry(const OrientedArgs &a, float eta, int32_t i, StagedEntry &st,
-                                             float2 &yi, float &en) {
+// on return st.yj, st.v1 and st.v2 hold the values this lane wrote.  LATER:
+// the first negatives of (j, i) are gathered after the whole step (i, j),
+// then the later groups of each direction follow it (later_direct).
+template <bool RED, int G, bool E, bool LATER = false>
+__device__ __forceinline__ void finish_entry(const OrientedArgs &a, const GraphCtx &c, int32_t i, StagedEntry &st,
+                                             float2 &yi, float &en, const StagedEntry &nxt, int32_t row_n,
+                                             bool track, uint32_t &stale) {
+    const float eta = c.eta;
     float2 yj = st.yj;
     const float2 yj0 = yj;
     {
@@ -381,6 +430,7 @@ __device__ __forceinline__ void finish_entry(const OrientedArgs &a, float eta, i
         yj.x -= df.x;
         yj.y -= df.y;
         if (G > 0) negative_group<RED, E>(a.pos, eta, st.s1, st.v1, G, yi, st.j, yj, en);
+        if (LATER) later_direct<RED, E>(a, c, st.e1, i, yi, st.j, yj, nxt, row_n, track, stale, en);
     }
     {
         if (E) en += attraction_energy(yj.x - yi.x, yj.y - yi.y);
@@ -391,13 +441,20 @@ __device__ __forceinline__ void finish_entry(const OrientedArgs &a, float eta, i
         yi.x -= df.x;
         yi.y -= df.y;
         if (G > 0) {
+            if (LATER) {
+                // gathered now: memory holds every update of the step (i, j)
 #pragma unroll
-            for (int m = 0; m < G; ++m)
+                for (int m = 0; m < G; ++m) st.v2[m] = load_pos(a.pos + st.s2[m]);
+            } else {
 #pragma unroll
-                for (int q = 0; q < G; ++q)
-                    if (st.s1[q] == st.s2[m]) st.v2[m] = st.v1[q];
+                for (int m = 0; m < G; ++m)
+#pragma unroll
+                    for (int q = 0; q < G; ++q)
+                        if (st.s1[q] == st.s2[m]) st.v2[m] = st.v1[q];
+            }
             negative_group<RED, E>(a.pos, eta, st.s2, st.v2, G, yj, i, yi, en);
         }
+        if (LATER) later_direct<RED, E>(a, c, st.e2, st.j, yj, i, yi, nxt, row_n, track, stale, en);
     }
     const float2 dj = make_float2(__fsub_rn(yj.x, yj0.x), __fsub_rn(yj.y, yj0.y));
     apply_partner<RED>(a.pos, st.j, yj, dj);
@@ -423,13 +480,16 @@ __device__ __forceinline__ float2 forwarded(int32_t x, float2 v, const StagedEnt
     return v;
 }
 
-template <int G>
+// LATER: next.v2 is not staged (it is gathered when it is applied).
+template <int G, bool LATER = false>
 __device__ __forceinline__ void forward_into(StagedEntry &next, const StagedEntry &done, int32_t i, float2 yi_mem) {
     next.yj = forwarded<G>(next.j, next.yj, done, i, yi_mem);
 #pragma unroll
     for (int m = 0; m < G; ++m) next.v1[m] = forwarded<G>(next.s1[m], next.v1[m], done, i, yi_mem);
+    if (!LATER) {
 #pragma unroll
-    for (int m = 0; m < G; ++m) next.v2[m] = forwarded<G>(next.s2[m], next.v2[m], done, i, yi_mem);
+        for (int m = 0; m < G; ++m) next.v2[m] = forwarded<G>(next.s2[m], next.v2[m], done, i, yi_mem);
+    }
 }
 
 // The value the source write-back leaves in memory for this lane's view
@@ -445,8 +505,8 @@ __device__ __forceinline__ float2 written_source(const OrientedArgs &a, float2 y
 }
 
 // ---------------------------------------------------------------------------
-// Direct chunk walk (the default with uniform negatives and k <= 4, for
-// single graphs, batches and multi-handle epochs).  Every entry names its
+// Direct chunk walk (the default with uniform negatives, for single graphs,
+// batches and multi-handle epochs).  Every entry names its
 // source, so a lane needs no row offsets: the first entry of a chunk gives
 // the row, and a change of source in a later entry is a row change (in a
 // batch, the graph is looked up then).  The next entry's words are drawn and
@@ -462,7 +522,7 @@ __device__ __forceinline__ float2 written_source(const OrientedArgs &a, float2 y
 #define SNAP_DIRECT 1
 #endif
 
-template <bool RED, int G, bool MULTI>
+template <bool RED, int G, bool MULTI, bool LATER = false>
 __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, const GraphCtx &c0, int64_t slot,
                                                       int4 ent0, int2 mt, uint32_t &flags) {
     const int64_t step = chunk_group_width(slot, a.num_segs);
@@ -475,7 +535,8 @@ __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, con
     float2 yi = load_pos(a.pos + row);
     int32_t pieces = RED ? __ldg(a.pieces + row) : 1;
     StagedEntry cur, nxt;
-    if (c.active) stage_entry<G>(a, c, row, ent0, cur);
+    nxt.j = -1;
+    if (c.active) stage_entry<G, LATER>(a, c, row, ent0, cur);
     int4 ent_next = len > 1 ? load_entry(ep + step) : ent0;
     float2 yi0 = yi;
     for (int32_t q = 0; q < len; ++q) {
@@ -490,10 +551,13 @@ __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, con
                 if (RED) pieces_n = __ldg(a.pieces + row_n);
                 if (MULTI) c_n = graph_ctx<true>(a, row_n);
             }
-            if (c_n.active) stage_entry<G>(a, c_n, row_n, ent_next, nxt);
+            if (c_n.active) stage_entry<G, LATER>(a, c_n, row_n, ent_next, nxt);
             if (q + 2 < len) ent_next = load_entry(ep + (int64_t)(q + 2) * step);
         }
-        if (c.active) finish_entry<RED, G, false>(a, c.eta, row, cur, yi, en);
+        uint32_t stale = 0;
+        if (c.active)
+            finish_entry<RED, G, false, LATER>(a, c, row, cur, yi, en, nxt, row_n != row ? row_n : -1,
+                                               more && c_n.active, stale);
         if (!more) break;
         if (row_n != row) {
             if (c.active) {
@@ -501,7 +565,7 @@ __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, con
                 const float2 mem = written_source<RED>(a, yi, yi0, pieces);
                 if (c_n.active) {
                     yi_n = forwarded<G>(row_n, yi_n, cur, row, mem);
-                    forward_into<G>(nxt, cur, row, mem);
+                    forward_into<G, LATER>(nxt, cur, row, mem);
                 }
             }
             row = row_n;
@@ -510,7 +574,15 @@ __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, con
             yi0 = yi;
             pieces = pieces_n;
         } else if (c.active) {
-            forward_into<G>(nxt, cur, row, yi);
+            forward_into<G, LATER>(nxt, cur, row, yi);
+        }
+        if (LATER && stale) {
+            // written by a later negative after they were gathered: gather again
+            if (stale & 1u) nxt.yj = load_pos(a.pos + nxt.j);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (stale & (2u << m)) nxt.v1[m] = load_pos(a.pos + nxt.s1[m]);
+            if (stale & 32u) yi = yi0 = load_pos(a.pos + row);
         }
         cur = nxt;
     }
@@ -519,7 +591,7 @@ __device__ __forceinline__ void oriented_chunk_direct(const OrientedArgs &a, con
 
 // The lanes' slot loop of the direct walk: the next chunk's first entry and
 // descriptor are in flight while the current chunk is walked.
-template <bool RED, int G, bool MULTI>
+template <bool RED, int G, bool MULTI, bool LATER = false>
 __device__ __forceinline__ void direct_slots(const OrientedArgs &a, uint32_t &flags) {
     const int64_t groups = (a.num_segs + 31) >> 5;
     const int64_t limit = groups << 5;
@@ -542,7 +614,7 @@ __device__ __forceinline__ void direct_slots(const OrientedArgs &a, uint32_t &fl
             ent2 = load_entry(a.ent + chunk_entry_index(ws2, a.num_segs, a.seg_len, 0));
             mt2 = __ldg(a.meta + ws2);
         }
-        if (ws < a.num_segs) oriented_chunk_direct<RED, G, MULTI>(a, c, ws, ent0, mt, flags);
+        if (ws < a.num_segs) oriented_chunk_direct<RED, G, MULTI, LATER>(a, c, ws, ent0, mt, flags);
         w = w2;
         ws = ws2;
         ent0 = ent2;
@@ -554,12 +626,21 @@ __device__ __forceinline__ void direct_slots(const OrientedArgs &a, uint32_t &fl
 // looked up again at every row change.  E: also sum the actual energy of the
 // epoch (half the sum over the directed steps of U^a and over the drawn pairs
 // of U^r, each at the moment of its update) into *a.energy.
-template <bool RED, int G, bool MULTI, bool W, bool E>
+//
+// GW is the kernel's negative width: G = min(GW, 4) negatives per direction
+// are drawn and gathered together; GW = 5 is the direct walk for k > 4 (the
+// first four staged, later groups of four gathered when applied), kept in
+// kernels of its own so that it costs the k <= 4 kernels no registers.
+template <int GW>
+__host__ __device__ constexpr int group_width() { return GW > 4 ? 4 : GW; }
+
+template <bool RED, int GW, bool MULTI, bool W, bool E>
 __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_kernel(const OrientedArgs a) {
+    constexpr int G = group_width<GW>();
     uint32_t flags = 0;
     double energy = 0.0;
-    if (SNAP_DIRECT && !W && !E && a.k <= 4 && (!RED || a.pieces)) {
-        direct_slots<RED, G, MULTI>(a, flags);
+    if (SNAP_DIRECT && !W && !E && (!RED || a.pieces)) {
+        direct_slots<RED, G, MULTI, (GW > 4)>(a, flags);
         if (flags) atomicOr(a.status, flags);
         return;
     }
@@ -586,8 +667,9 @@ __global__ void __launch_bounds__(256, SNAP_ORIENTED_MIN_BLOCKS) oriented_epoch_
 #ifndef SNAP_MULTI_MIN_BLOCKS
 #define SNAP_MULTI_MIN_BLOCKS 1
 #endif
-template <bool RED, int G, bool WEIGHTED>
+template <bool RED, int GW, bool WEIGHTED>
 __global__ void __launch_bounds__(256, SNAP_MULTI_MIN_BLOCKS) multi_epoch_kernel(const MultiArgs m) {
+    constexpr int G = group_width<GW>();
     uint32_t flags = 0;
     const int64_t groups = (m.total_segs + 31) >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -627,10 +709,10 @@ __global__ void __launch_bounds__(256, SNAP_MULTI_MIN_BLOCKS) multi_epoch_kernel
         const int64_t slot = ws - jd.seg_prefix;
         if (WEIGHTED && G > 0 && a.alias) {
             oriented_chunk<RED, G, false, true, false>(a, slot, flags, en);
-        } else if (SNAP_DIRECT && a.k <= 4 && (!RED || a.pieces)) {
+        } else if (SNAP_DIRECT && (!RED || a.pieces)) {
             const int4 ent0 = load_entry(a.ent + chunk_entry_index(slot, a.num_segs, a.seg_len, 0));
             const int2 mt = __ldg(a.meta + slot);
-            oriented_chunk_direct<RED, G, false>(a, graph_ctx<false>(a, 0), slot, ent0, mt, flags);
+            oriented_chunk_direct<RED, G, false, (GW > 4)>(a, graph_ctx<false>(a, 0), slot, ent0, mt, flags);
         } else {
             oriented_chunk<RED, G, false, false, false>(a, slot, flags, en);
         }
@@ -764,15 +846,25 @@ __global__ void __launch_bounds__(256) sync_apply_kernel(float2 *pos, long long 
     if (flags) atomicOr(status, flags);
 }
 
-// Launch and occupancy helpers over the negative-group width G = min(k, 4).
+// Launch and occupancy helpers over the negative width GW: min(k, 4), or 5
+// for k > 4 where the kernel takes the direct walk (uniform negatives, no
+// energy); the weighted and energy kernels handle k > 4 at width 4.
+template <bool W, bool E>
+inline int negative_width(int k) {
+    return k <= 4 ? k : (!W && !E ? 5 : 4);
+}
+
 template <bool RED, bool MULTI, bool W, bool E>
 cudaError_t launch_oriented_k(const OrientedArgs &a, int grid, int block, cudaStream_t s) {
-    switch (a.k < 4 ? a.k : 4) {
+    switch (negative_width<W, E>(a.k)) {
         case 0: oriented_epoch_kernel<RED, 0, MULTI, false, E><<<grid, block, 0, s>>>(a); break;
         case 1: oriented_epoch_kernel<RED, 1, MULTI, W, E><<<grid, block, 0, s>>>(a); break;
         case 2: oriented_epoch_kernel<RED, 2, MULTI, W, E><<<grid, block, 0, s>>>(a); break;
         case 3: oriented_epoch_kernel<RED, 3, MULTI, W, E><<<grid, block, 0, s>>>(a); break;
-        default: oriented_epoch_kernel<RED, 4, MULTI, W, E><<<grid, block, 0, s>>>(a); break;
+        case 4: oriented_epoch_kernel<RED, 4, MULTI, W, E><<<grid, block, 0, s>>>(a); break;
+        default:
+            if constexpr (!W && !E) oriented_epoch_kernel<RED, 5, MULTI, false, false><<<grid, block, 0, s>>>(a);
+            break;
     }
     return cudaGetLastError();
 }
@@ -786,35 +878,42 @@ int occupancy_of(K kernel, int block) {
 
 template <bool RED, bool MULTI, bool W, bool E>
 int oriented_occupancy_k(int k, int block) {
-    switch (k < 4 ? k : 4) {
+    switch (negative_width<W, E>(k)) {
         case 0: return occupancy_of(oriented_epoch_kernel<RED, 0, MULTI, false, E>, block);
         case 1: return occupancy_of(oriented_epoch_kernel<RED, 1, MULTI, W, E>, block);
         case 2: return occupancy_of(oriented_epoch_kernel<RED, 2, MULTI, W, E>, block);
         case 3: return occupancy_of(oriented_epoch_kernel<RED, 3, MULTI, W, E>, block);
-        default: return occupancy_of(oriented_epoch_kernel<RED, 4, MULTI, W, E>, block);
+        case 4: return occupancy_of(oriented_epoch_kernel<RED, 4, MULTI, W, E>, block);
+        default:
+            if constexpr (!W && !E) return occupancy_of(oriented_epoch_kernel<RED, 5, MULTI, false, false>, block);
+            return 1;
     }
 }
 
+// The multi-handle kernel takes width 5 for k > 4 also when some jobs draw
+// weighted negatives (those jobs walk their chunks at width 4).
 template <bool RED, bool WEIGHTED>
 cudaError_t launch_multi_k(const MultiArgs &a, int grid, int block, cudaStream_t s) {
-    switch (a.k < 4 ? a.k : 4) {
+    switch (negative_width<false, false>(a.k)) {
         case 0: multi_epoch_kernel<RED, 0, false><<<grid, block, 0, s>>>(a); break;
         case 1: multi_epoch_kernel<RED, 1, WEIGHTED><<<grid, block, 0, s>>>(a); break;
         case 2: multi_epoch_kernel<RED, 2, WEIGHTED><<<grid, block, 0, s>>>(a); break;
         case 3: multi_epoch_kernel<RED, 3, WEIGHTED><<<grid, block, 0, s>>>(a); break;
-        default: multi_epoch_kernel<RED, 4, WEIGHTED><<<grid, block, 0, s>>>(a); break;
+        case 4: multi_epoch_kernel<RED, 4, WEIGHTED><<<grid, block, 0, s>>>(a); break;
+        default: multi_epoch_kernel<RED, 5, WEIGHTED><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
 template <bool RED, bool WEIGHTED>
 int multi_occupancy_k(int k, int block) {
-    switch (k < 4 ? k : 4) {
+    switch (negative_width<false, false>(k)) {
         case 0: return occupancy_of(multi_epoch_kernel<RED, 0, false>, block);
         case 1: return occupancy_of(multi_epoch_kernel<RED, 1, WEIGHTED>, block);
         case 2: return occupancy_of(multi_epoch_kernel<RED, 2, WEIGHTED>, block);
         case 3: return occupancy_of(multi_epoch_kernel<RED, 3, WEIGHTED>, block);
-        default: return occupancy_of(multi_epoch_kernel<RED, 4, WEIGHTED>, block);
+        case 4: return occupancy_of(multi_epoch_kernel<RED, 4, WEIGHTED>, block);
+        default: return occupancy_of(multi_epoch_kernel<RED, 5, WEIGHTED>, block);
     }
 }
 

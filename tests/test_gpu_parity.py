@@ -102,7 +102,7 @@ def test_single_lane_hogwild_is_algorithm1_in_oriented_order(cuda, mode, n, m, k
 
 
 @pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
-@pytest.mark.parametrize("n,m,k", [(40, 120, 3), (300, 900, 4)])
+@pytest.mark.parametrize("n,m,k", [(40, 120, 3), (300, 900, 4), (90, 300, 7)])
 def test_single_lane_hogwild_with_ascending_rows(cuda, mode, n, m, k):
     """The row order the autotuner may choose (entries of a row in ascending
     partner id): one lane is Algorithm 1 in that order.  Also after the

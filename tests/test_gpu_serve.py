@@ -23,7 +23,8 @@ def _alone(torch, g, Y0, epochs, k, sched, seed, seg=0):
     return pos.cpu().numpy()
 
 
-def test_multi_epoch_equals_separate_launches_with_staggered_starts(cuda):
+@pytest.mark.parametrize("k", [3, 7])
+def test_multi_epoch_equals_separate_launches_with_staggered_starts(cuda, k):
     torch = cuda
     graphs = [tiny_graph(300, 900, seed=s) for s in (1, 2, 3)]
     starts = [0, 3, 5]                      # jobs join at different ticks
@@ -37,14 +38,14 @@ def test_multi_epoch_equals_separate_launches_with_staggered_starts(cuda):
         for tick in range(13):
             jobs = [(handles[q], pos[q], tick - starts[q], sched, 40 + q) for q in range(3)
                     if 0 <= tick - starts[q] < 8]
-            multi.epoch(jobs, 3)
+            multi.epoch(jobs, k)
         multi.check()
     finally:
         multi.close()
         for h in handles:
             snap.snap_layout_destroy(h)
     for q, g in enumerate(graphs):
-        alone = _alone(torch, g, Y0[q], 8, 3, sched, 40 + q, seg=ONE_LANE)
+        alone = _alone(torch, g, Y0[q], 8, k, sched, 40 + q, seg=ONE_LANE)
         assert np.array_equal(pos[q].cpu().numpy().view(np.uint32), alone.view(np.uint32)), q
 
 
