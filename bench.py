@@ -140,17 +140,19 @@ def probe_rates(nbytes, stream):
     import torch
     lib = probe_library()
     nbytes = max(32, (int(nbytes) + 15) // 16 * 16)
-    buf = torch.zeros(nbytes // 4, dtype=torch.float32, device="cuda")
+    # ops 0-3 use the first nbytes; op 4 also a displacement array twice that size after it
+    buf = torch.zeros(3 * nbytes // 4, dtype=torch.float32, device="cuda")
     sink = torch.zeros(1, dtype=torch.float32, device="cuda")
     sms = torch.cuda.get_device_properties(buf.device).multi_processor_count
     out = {}
     for name, op, iters, grid in (("l2_read_bytes_per_s", 0, 16, sms * 8), ("random_loads_per_s", 1, 16, sms * 8),
                                   ("random_atomic_adds_per_s", 2, 16, sms * 8),
-                                  ("random_load_atomic_pairs_per_s", 3, 16, sms * 8)):
+                                  ("random_load_atomic_pairs_per_s", 3, 16, sms * 8),
+                                  ("random_load_int64_atomic_triples_per_s", 4, 16, sms * 8)):
         best = 0.0
         for _ in range(2):
-            r = lib.bench_probe_rate(ctypes.c_void_p(buf.data_ptr()), nbytes, op, iters, grid,
-                                     ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+            r = lib.bench_probe_rate(ctypes.c_void_p(buf.data_ptr()), 3 * nbytes if op == 4 else nbytes, op, iters,
+                                     grid, ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
             if r < 0:
                 raise RuntimeError(f"bench_probe_rate op {op} failed ({r})")
             best = max(best, r)
@@ -340,6 +342,13 @@ def rooflines(nnz, n, k, launch_ms, probes, peak_hbm, peak_kind, traffic, kernel
             ops["mixed_frac"] = t_mix / launch_s
             ops["mixed_note"] = ("the same loads and atomic adds interleaved without dependence (bench_probe.cu op 3): "
                                  "the ceiling of this access mix")
+        if sync and probes.get("random_load_int64_atomic_triples_per_s"):
+            t_mix = n_ops / probes["random_load_int64_atomic_triples_per_s"]
+            ops["mixed_triple_peak_per_s"] = probes["random_load_int64_atomic_triples_per_s"]
+            ops["mixed_bound_ms"] = t_mix * 1e3
+            ops["mixed_frac"] = t_mix / launch_s
+            ops["mixed_note"] = ("each term's random position load interleaved with its two int64 atomic adds to a "
+                                 "separate displacement array, without dependence (bench_probe.cu op 4)")
     binding = hbm
     if l2 and l2_bytes / (l2["peak"] * 1e9) > hbm_bytes / (peak_hbm * 1e9):
         binding = l2
@@ -548,6 +557,11 @@ def run_snap(args, rank, world, local_rank):
              if mode != snap.MODE_SYNC else "sync epoch (sync_chunk_kernel + sync_apply_kernel)")
     roofs = rooflines(nnz, n, k, float(np.mean(launch_ms)), probes, peak, peak_kind,
                       recorded_traffic(args.mode, k), kname, sync=mode == snap.MODE_SYNC)
+    if probes and "mode_sync" in extras:
+        # the whole synchronous epoch (16 chunk launches + 16 applies) against its access mix's ceiling
+        t_mix = nnz * (1 + k) / probes["random_load_int64_atomic_triples_per_s"]
+        extras["mode_sync"]["mixed_bound_ms"] = t_mix * 1e3
+        extras["mode_sync"]["mixed_frac"] = t_mix * 1e3 / extras["mode_sync"]["ms_per_epoch"]
     deg = np.diff(row_ptr)
     nonempty = int((deg > 0).sum())
 

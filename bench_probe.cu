@@ -18,6 +18,12 @@
 //         random atomic adds to other slots, independent of each other (the
 //         mix the epoch kernels issue, without their dependence); load +
 //         atomic pairs per second
+//   op 4  the synchronous mode's mix: the array is cut into a position part
+//         (its first third, 8-byte slots) and a displacement part (the rest,
+//         16-byte slots of two int64); per thread and iteration 8 random
+//         position loads and 8 random displacement slots, each given two
+//         64-bit integer atomic adds (atom.global.add.u64, no return);
+//         load + two-atomic triples per second
 // Slots come from a 64-bit mixing hash of (thread, iteration) reduced to
 // [0, n) by a multiply-shift, so every access stays inside the array.
 #include <cuda_runtime.h>
@@ -92,16 +98,38 @@ __global__ void __launch_bounds__(256) random_mixed_kernel(float2 *a, uint32_t n
     if (acc == 12345.678f) sink[0] = acc;
 }
 
+__global__ void __launch_bounds__(256) random_sync_mixed_kernel(const float2 *a, uint32_t n,
+                                                                unsigned long long *disp, uint32_t nd, int iters,
+                                                                float *sink) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    for (int it = 0; it < iters; ++it) {
+        float2 v[kDepth];
+#pragma unroll
+        for (int d = 0; d < kDepth; ++d) v[d] = __ldcg(a + mix_slot((tid << 24) ^ ((uint64_t)it * kDepth + d), n));
+#pragma unroll
+        for (int q = 0; q < kDepth; ++q) {
+            unsigned long long *p =
+                disp + 2 * (uint64_t)mix_slot(((tid << 24) ^ ((uint64_t)it * kDepth + q)) + 0x9E37ull, nd);
+            atomicAdd(p, 1ull);
+            atomicAdd(p + 1, 1ull);
+        }
+#pragma unroll
+        for (int q = 0; q < kDepth; ++q) acc += v[q].x;
+    }
+    if (acc == 12345.678f) sink[0] = acc;
+}
+
 }  // namespace
 
 // Runs probe `op` (above) on the caller's device array `a` of `bytes` bytes
-// (a multiple of 16, at least 32) with `grid` blocks of 256 threads, once to
+// (a multiple of 16, at least 48) with `grid` blocks of 256 threads, once to
 // warm up and once timed with CUDA events on `cuda_stream`.  `sink` is one
 // device float.  Returns the op's rate (bytes/s for op 0, accesses/s
 // otherwise) or a negative value on error.
 extern "C" double bench_probe_rate(float *a, int64_t bytes, int op, int iters, int grid, float *sink,
                                    void *cuda_stream) {
-    if (!a || !sink || bytes < 32 || (bytes & 15) != 0 || op < 0 || op > 3 || iters <= 0 || grid <= 0) return -1.0;
+    if (!a || !sink || bytes < 48 || (bytes & 15) != 0 || op < 0 || op > 4 || iters <= 0 || grid <= 0) return -1.0;
     const int64_t n2 = bytes / 8;
     if (n2 > 0xFFFFFFFFll) return -1.0;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -120,8 +148,15 @@ extern "C" double bench_probe_rate(float *a, int64_t bytes, int op, int iters, i
             random_load_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(a), (uint32_t)n2, iters, sink);
         else if (op == 2)
             random_red_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<float2 *>(a), (uint32_t)n2, iters);
-        else
+        else if (op == 3)
             random_mixed_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<float2 *>(a), (uint32_t)n2, iters, sink);
+        else {
+            const int64_t pos_bytes = bytes / 48 * 16;   // a third, a multiple of 16
+            random_sync_mixed_kernel<<<grid, 256, 0, s>>>(
+                reinterpret_cast<const float2 *>(a), (uint32_t)(pos_bytes / 8),
+                reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(a) + pos_bytes),
+                (uint32_t)((bytes - pos_bytes) / 16), iters, sink);
+        }
         err = cudaGetLastError();
     }
     cudaEventRecord(e1, s);

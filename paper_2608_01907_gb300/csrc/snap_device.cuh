@@ -190,6 +190,21 @@ __device__ __forceinline__ int32_t weighted_in(const GraphCtx &c, WordCursor &wc
     return c.base + weighted_negative(wc, c.epoch, c.key, alias + c.base, c.nm1 + 1u, src - c.base);
 }
 
+// One pair's term in the synchronous mode: the force on the source i from
+// the attraction (REP = false) or the repulsion (REP = true) of Table 1 at
+// the frozen positions, quantised (to_fixed); the source's share is summed
+// into accx / accy, the other vertex's is added to disp.
+template <bool REP>
+__device__ __forceinline__ void sync_pair_term(long long *disp, float2 yi, int32_t x, float2 yx, long long &accx,
+                                               long long &accy, uint32_t &flags) {
+    const float2 f = REP ? repulsion_on_i(yi.x - yx.x, yi.y - yx.y) : attraction_on_i(yi.x - yx.x, yi.y - yx.y);
+    const long long fx = to_fixed(f.x, flags), fy = to_fixed(f.y, flags);
+    accx += fx;
+    accy += fy;
+    add_fixed(disp + 2 * (int64_t)x, -fx);
+    add_fixed(disp + 2 * (int64_t)x + 1, -fy);
+}
+
 // All force terms of directed edge e = (i, j) in the synchronous mode, with
 // positions frozen (read-only during the launch): the attraction of Table 1
 // and the repulsion of each of its k negatives (Algorithm 1's draws, in the
@@ -208,12 +223,7 @@ __device__ __forceinline__ float sync_edge_terms(const float2 *pos, long long *d
     const float2 yj = __ldg(pos + j);
     float en = 0.0f;
     if (energy) en += attraction_energy(yi.x - yj.x, yi.y - yj.y);
-    const float2 f = attraction_on_i(yi.x - yj.x, yi.y - yj.y);
-    const long long fx = to_fixed(f.x, flags), fy = to_fixed(f.y, flags);
-    accx += fx;
-    accy += fy;
-    add_fixed(disp + 2 * (int64_t)j, -fx);
-    add_fixed(disp + 2 * (int64_t)j + 1, -fy);
+    sync_pair_term<false>(disp, yi, j, yj, accx, accy, flags);
     WordCursor wc = cursor_in(c, e);
     for (int g = 0; g * 4 < k; ++g) {
         const int nm = k - 4 * g < 4 ? k - 4 * g : 4;
@@ -236,12 +246,7 @@ __device__ __forceinline__ float sync_edge_terms(const float2 *pos, long long *d
         for (int m = 0; m < 4; ++m) {
             if (m < nm) {
                 if (energy) en += repulsion_energy(yi.x - ys[m].x, yi.y - ys[m].y);
-                const float2 gr = repulsion_on_i(yi.x - ys[m].x, yi.y - ys[m].y);
-                const long long gx = to_fixed(gr.x, flags), gy = to_fixed(gr.y, flags);
-                accx += gx;
-                accy += gy;
-                add_fixed(disp + 2 * (int64_t)s[m], -gx);
-                add_fixed(disp + 2 * (int64_t)s[m] + 1, -gy);
+                sync_pair_term<true>(disp, yi, s[m], ys[m], accx, accy, flags);
             }
         }
     }

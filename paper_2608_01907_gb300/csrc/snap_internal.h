@@ -69,9 +69,10 @@ struct SyncArgs {
     double *energy;              // actual energy of the epoch is added here (null: not computed)
 };
 
-// Oriented bundle list: entry {j, low 32 bits of the CSR indices of (i, j)
-// and (j, i), bits 32..47 of both} for each partner j ranked below i,
-// row-major (rows in vertex order, a row's entries in affine order).  The
+// Oriented bundle list: entry {j, CSR index of (i, j), CSR index of (j, i),
+// i} (indices as unsigned 32-bit) for each partner j ranked below i,
+// row-major (rows in vertex order, a row's entries in affine or ascending
+// partner order).  The
 // list is cut into chunks of T consecutive entries (a chunk may cross row
 // boundaries; the last one may be short); chunk c goes to slot
 // (mul * c + add) mod S, S = ceil(nnz / T), so neighbouring slots hold

@@ -2,7 +2,7 @@
 graph whose positions do not fit in L2 -- R-MAT 2^25 nodes / 268,435,456
 undirected edges (the native generator, seed 1, BFS locality relabelling;
 positions 268 MB) -- scored; the stored side of
-tests/test_gpu_quality_rmat25.py.
+tests/test_gpu_past_l2.py.
 
 Each layout is Algorithm 1 in the oracle (FP64, edge list shuffled once),
 k = 3, 30 epochs, linear step decay from eta0 = 1 (floor 1e-3 eta0), seeds

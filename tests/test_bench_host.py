@@ -77,3 +77,7 @@ def test_rooflines_follow_their_definitions():
     r = bench.rooflines(nnz, n, k, ms, probes, 6689.1, "measured", None, "kernel", sync=True)
     assert r["l2"]["algorithmic_bytes_per_launch"] == 96 * (k + 1) * nnz
     assert r["ops"]["atomic_adds_per_launch"] == 2 * ops and "mixed_frac" not in r["ops"]
+    # ... and its mix is one load and two integer atomics per term (probe op 4)
+    probes["random_load_int64_atomic_triples_per_s"] = 50e9
+    r = bench.rooflines(nnz, n, k, ms, probes, 6689.1, "measured", None, "kernel", sync=True)
+    assert abs(r["ops"]["mixed_frac"] - ops / 50e9 / (ms / 1e3)) < 1e-12
