@@ -45,7 +45,7 @@ def test_weighted_sync_matches_oracle_after_one_epoch(cuda, kind, name, k, S):
 
 @pytest.mark.parametrize("kind", ["degree", "weights"])
 @pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
-@pytest.mark.parametrize("n,m,k", [(12, 30, 5), (90, 300, 10), (300, 900, 3)])
+@pytest.mark.parametrize("n,m,k", [(12, 30, 5), (90, 300, 10), (300, 900, 3), (40, 120, 2), (90, 300, 4)])
 def test_weighted_single_lane_is_algorithm1_in_oriented_order(cuda, kind, mode, n, m, k):
     g = tiny_graph(n, m, seed=n)
     kw, sam = _sampler_pair(kind, g, seed=n)
@@ -126,7 +126,8 @@ def test_degree_batch_sync_equals_graphs_alone_bitwise(cuda):
     assert r == pytest.approx(rep, rel=1e-5)
 
 
-def test_degree_job_in_a_multi_epoch_equals_alone_bitwise(cuda):
+@pytest.mark.parametrize("k", [3, 6])
+def test_degree_job_in_a_multi_epoch_equals_alone_bitwise(cuda, k):
     torch = cuda
     graphs = [tiny_graph(300, 900, seed=s) for s in (1, 2)]
     sched = snap.linear_schedule(eta0=0.7, total_epochs=6)
@@ -139,13 +140,13 @@ def test_degree_job_in_a_multi_epoch_equals_alone_bitwise(cuda):
     multi = snap.MultiEpoch(4)
     try:
         for t in range(6):
-            multi.epoch([(handles[q], pos[q], t, sched, 40 + q) for q in range(2)], 6)
+            multi.epoch([(handles[q], pos[q], t, sched, 40 + q) for q in range(2)], k)
         multi.check()
     finally:
         multi.close()
         for h in handles:
             snap.snap_layout_destroy(h)
     for q, g in enumerate(graphs):
-        alone = gpu_layout(torch, g, Y0[q], 6, 6, sched, 40 + q,
+        alone = gpu_layout(torch, g, Y0[q], 6, k, sched, 40 + q,
                            opts=snap.make_options(segment_edges=4096, sampler=samplers[q]))
         assert np.array_equal(pos[q].cpu().numpy().view(np.uint32), alone.view(np.uint32)), q
