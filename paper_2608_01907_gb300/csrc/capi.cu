@@ -212,8 +212,8 @@ struct snap_layout {
     bool status_pending = false;
     int sms = 1;
     int grid_sync = 0, grid_apply = 0;
-    int grid_oriented[2][5] = {{0}};   // [red][min(k, 4)], filled on first use
-    int grid_energy[2][5] = {{0}};     // the same for epochs that sum the actual energy
+    int grid_oriented[2][6] = {{0}};   // [red][negative width: k if k <= 4, else 5], filled on first use
+    int grid_energy[2][6] = {{0}};     // the same for epochs that sum the actual energy
     std::vector<int64_t> chunk_edges;   // S + 1 edge offsets of the sync chunks
     int64_t device_bytes = 0;
     // CUDA graphs of captured epoch sequences (SNAP_FLAG_CUDA_GRAPH)
@@ -878,7 +878,7 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
             a.energy = energy ? energy + ep : nullptr;
             a.pieces = h->d_act_pieces;
             const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
-            const int g = neg_samples < 4 ? neg_samples : 4;
+            const int g = neg_samples <= 4 ? neg_samples : 5;   // the kernels' negative width
             const int gmax = energy ? h->grid_energy[red][g] : h->grid_oriented[red][g];
             if (gmax <= 0) return cudaErrorInvalidConfiguration;   // the caller sizes the grid first
             if (h->act_num_segs == 0) continue;
@@ -901,7 +901,7 @@ static cudaError_t enqueue_epochs(snap_layout *h, float2 *pos, int32_t epoch_beg
 // stream capture).
 static void resident_grid(snap_layout *h, int32_t neg_samples) {
     const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
-    const int g = neg_samples < 4 ? neg_samples : 4;
+    const int g = neg_samples <= 4 ? neg_samples : 5;   // the kernels' negative width
     if (h->grid_oriented[red][g] == 0)
         h->grid_oriented[red][g] =
             h->sms * oriented_blocks_per_sm(red, neg_samples, h->block, h->num_graphs > 1, h->d_alias != nullptr);
@@ -958,7 +958,7 @@ static snap_status epochs_impl(snap_layout_t h, float *positions, int32_t epoch_
     if (h->opts.mode != SNAP_MODE_SYNC) {
         // occupancy query outside any capture
         const int red = h->opts.mode == SNAP_MODE_HOGWILD_RED;
-        const int g = neg_samples < 4 ? neg_samples : 4;
+        const int g = neg_samples <= 4 ? neg_samples : 5;   // the kernels' negative width
         resident_grid(h, neg_samples);
         if (energy && h->grid_energy[red][g] == 0)
             h->grid_energy[red][g] =
@@ -1490,7 +1490,7 @@ struct snap_multi {
     cudaEvent_t copied = nullptr;
     bool copy_pending = false;
     int sms = 1;
-    int grid[2][2][5] = {{{0}}};   // [red][weighted][min(k, 4)], filled on first use
+    int grid[2][2][6] = {{{0}}};   // [red][weighted][negative width: k if k <= 4, else 5], filled on first use
     uint64_t calls = 0;
 
     void release() {
@@ -1604,7 +1604,7 @@ snap_status snap_multi_epoch(snap_multi_t m, const snap_layout_t *handles, float
     a.perm_mul = golden_multiplier(groups);
     a.perm_add = (int64_t)(mixkey % (uint64_t)groups);
     a.status = m->d_status;
-    const int g = neg_samples < 4 ? neg_samples : 4;
+    const int g = neg_samples <= 4 ? neg_samples : 5;   // the kernels' negative width
     int weighted = 0;
     for (int32_t q = 0; q < used; ++q) weighted |= m->h_jobs[q].alias != nullptr;
     if (m->grid[red][weighted][g] == 0)
