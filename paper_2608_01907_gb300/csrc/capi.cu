@@ -416,22 +416,25 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
              "orientation flags kernel");
         step(exclusive_scan_i32(temp, &temp_bytes, flags, pos, nnz + 1, stream), "orientation scan");
         step(launch_orient_scatter(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, pos,
-                                   h->d_act_ent, stream), "orientation scatter kernel");
+                                   h->d_act_ent, h->act_nnz, h->d_status + 1, stream),
+             "orientation scatter kernel");
         step(launch_orient_rowptr(h->d_row_ptr, pos, n, h->d_act_row_ptr, stream), "orientation offsets kernel");
     }
     int64_t total = -1;
     if (err == cudaSuccess) {
         step(cudaMemcpyAsync(&total, h->d_act_row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream),
              "read oriented entry count");
+        step(cudaMemcpyAsync(h->h_status + 1, h->d_status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream),
+             "read symmetry word");
         step(cudaStreamSynchronize(stream), "orientation");
     }
     if (flags) cudaFreeAsync(flags, stream);
     if (pos) cudaFreeAsync(pos, stream);
     if (temp) cudaFreeAsync(temp, stream);
     if (err != cudaSuccess) return cuda_fail(err, what);
-    if (total != h->act_nnz)
-        return fail(SNAP_ERR_CUDA, "orientation produced %lld entries, expected %lld", (long long)total,
-                    (long long)h->act_nnz);
+    // every owned edge has its reverse and half of the edges are owned: symmetric
+    if ((h->h_status[1] & kAsymmetric) || (nnz & 1) || total != h->act_nnz)
+        return fail(SNAP_ERR_INVALID_ARG, "the CSR is not symmetric: some (i, j) has no (j, i)");
     h->act_layout = ChunkLayout{0, 0, 0, 0};   // row-major, rows in the affine order of the scatter
     h->act_ent_bytes = 0;
     err = set_chunks(h, ac, h->act_seg_len, (h->opts.flags & SNAP_FLAG_ASCENDING_ROWS) ? 1 : 0, stream);
@@ -469,10 +472,9 @@ static snap_status check_csr_host(const int64_t *row_ptr, const int32_t *col_idx
     if (!row_ptr) return fail(SNAP_ERR_INVALID_ARG, "row_ptr is NULL");
     if (n < 1 || n == INT32_MAX) return fail(SNAP_ERR_INVALID_ARG, "n = %d out of range [1, 2^31-2]", n);
     if (row_ptr[0] != 0) return fail(SNAP_ERR_INVALID_ARG, "row_ptr[0] = %lld, expected 0", (long long)row_ptr[0]);
-    for (int32_t i = 0; i < n; ++i)
-        if (row_ptr[i + 1] < row_ptr[i])
-            return fail(SNAP_ERR_INVALID_ARG, "row_ptr decreases at row %d", i);
+    // the rest of row_ptr is checked on the device (check_row_ptr_kernel)
     const int64_t nnz = row_ptr[n];
+    if (nnz < 0) return fail(SNAP_ERR_INVALID_ARG, "row_ptr[n] = %lld is negative", (long long)nnz);
     if (nnz >= ((int64_t)1 << 32)) return fail(SNAP_ERR_INVALID_ARG, "nnz = %lld exceeds 2^32-1", (long long)nnz);
     if (nnz > 0 && !col_idx) return fail(SNAP_ERR_INVALID_ARG, "col_idx is NULL");
     if (degrees)
@@ -669,16 +671,26 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     }
     SNAP_CUDA(launch_segment_rows(h->d_row_ptr, n, h->nnz, h->seg_len, h->d_seg_row, h->num_segs, stream),
               "segment table kernel");
+    // symmetry: here for the synchronous mode, in the orientation pass otherwise
+    unsigned long long *upper = o.mode == SNAP_MODE_SYNC
+                                    ? reinterpret_cast<unsigned long long *>(h->d_status + 2)
+                                    : nullptr;
     SNAP_CUDA(launch_validate_csr(h->d_row_ptr, h->d_col, h->d_seg_row, n, h->nnz, h->seg_len, h->d_status + 1,
-                                  stream, h->d_node_graph), "validation kernel");
+                                  stream, h->d_node_graph, upper), "validation kernel");
     SNAP_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, stream),
               "read validation word");
     SNAP_CUDA(cudaStreamSynchronize(stream), "create");
 #undef SNAP_CUDA
-    const uint32_t vflags = h->h_status[1];
+    uint32_t vflags = h->h_status[1];
+    if (upper && !vflags) {
+        unsigned long long count = 0;
+        memcpy(&count, h->h_status + 2, sizeof(count));
+        if ((h->nnz & 1) || (int64_t)count != h->nnz / 2) vflags |= kAsymmetric;
+    }
     if (vflags) {
         h->release();
         delete h;
+        if (vflags & kBadRowPtr) return fail(SNAP_ERR_INVALID_ARG, "row_ptr decreases or leaves [0, nnz]");
         if (vflags & kBadColumn) return fail(SNAP_ERR_INVALID_ARG, "col_idx holds a column outside [0, n)");
         if (vflags & kSelfLoop) return fail(SNAP_ERR_INVALID_ARG, "col_idx holds a self-loop (j == i)");
         if (vflags & kUnsorted) return fail(SNAP_ERR_INVALID_ARG, "a row of col_idx is not strictly ascending");

@@ -31,19 +31,44 @@ __global__ void segment_rows_kernel(const int64_t *__restrict__ row_ptr, int32_t
     }
 }
 
-// deg[i] = row_ptr[i+1] - row_ptr[i] (row_ptr checked non-decreasing on the host).
+// deg[i] = row_ptr[i+1] - row_ptr[i] (row_ptr checked non-decreasing by
+// check_row_ptr_kernel before anything uses it as a rank).
 __global__ void degrees_kernel(const int64_t *__restrict__ row_ptr, int32_t n, int32_t *__restrict__ deg) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         deg[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
 }
 
+// row_ptr non-decreasing inside [0, nnz] (row_ptr[0] = 0 and row_ptr[n] =
+// nnz are checked on the host).  Every kernel that runs before this result
+// is read clamps the offsets it uses as indices.
+__global__ void check_row_ptr_kernel(const int64_t *__restrict__ row_ptr, int32_t n, int64_t nnz,
+                                     uint32_t *flags_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
+        if (lo < 0 || hi < lo || hi > nnz) bad = true;
+    }
+    if (bad) atomicOr(flags_out, kBadRowPtr);
+}
+
+// Columns in [0, n), no self-loop, rows strictly ascending, no edge across
+// two graphs of a batch.  upper_count != null (the synchronous mode, which
+// has no orientation pass): also symmetry, checked on half of the edges --
+// every (i, j) with j < i must have (j, i) in row j (binary search), and the
+// number of such edges must be nnz / 2 (the caller compares): reversal maps
+// them one-to-one into the edges with j > i, so equal counts mean every edge
+// has its reverse.  (The HOGWILD modes check symmetry the same way in the
+// orientation pass, which searches the reverse of half of the edges anyway.)
 __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                     const int32_t *__restrict__ seg_row, int32_t n, int64_t nnz,
-                                    int32_t seg_len, uint32_t *flags_out, const int32_t *__restrict__ node_graph) {
+                                    int32_t seg_len, uint32_t *flags_out, const int32_t *__restrict__ node_graph,
+                                    unsigned long long *upper_count) {
     const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t flags = 0;
+    unsigned long long upper = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
         const int64_t e0 = s * seg_len;
         const int64_t e1 = min(e0 + (int64_t)seg_len, nnz);
@@ -51,7 +76,7 @@ __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const i
         int64_t row_begin = row_ptr[row];
         int64_t row_end = row_ptr[row + 1];
         for (int64_t e = e0; e < e1; ++e) {
-            while (e >= row_end) {
+            while (e >= row_end && row < n - 1) {
                 ++row;
                 row_begin = row_end;
                 row_end = row_ptr[row + 1];
@@ -63,26 +88,30 @@ __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const i
             }
             if (j == row) flags |= kSelfLoop;
             if (node_graph && node_graph[j] != node_graph[row]) flags |= kCrossGraph;
-            if (e > row_begin && col_idx[e - 1] >= j) flags |= kUnsorted;
-            // symmetry: binary search for `row` in row j
-            int64_t lo = row_ptr[j], hi = row_ptr[j + 1];
-            bool found = false;
-            while (lo < hi) {
-                const int64_t mid = lo + (hi - lo) / 2;
-                const int32_t v = col_idx[mid];
-                if (v == row) {
-                    found = true;
-                    break;
+            if (e > row_begin && e > 0 && col_idx[e - 1] >= j) flags |= kUnsorted;
+            if (upper_count && j < row) {
+                ++upper;
+                // binary search for `row` in row j (offsets clamped to [0, nnz])
+                int64_t lo = max(row_ptr[j], (int64_t)0), hi = min(row_ptr[j + 1], nnz);
+                bool found = false;
+                while (lo < hi) {
+                    const int64_t mid = lo + (hi - lo) / 2;
+                    const int32_t v = col_idx[mid];
+                    if (v == row) {
+                        found = true;
+                        break;
+                    }
+                    if (v < row)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
                 }
-                if (v < row)
-                    lo = mid + 1;
-                else
-                    hi = mid;
+                if (!found) flags |= kAsymmetric;
             }
-            if (!found) flags |= kAsymmetric;
         }
     }
     if (flags) atomicOr(flags_out, flags);
+    if (upper_count && upper) atomicAdd(upper_count, upper);
 }
 
 // Orientation of the undirected edges: {i, j} belongs to the bundle of the
@@ -179,16 +208,24 @@ __device__ __forceinline__ int32_t row_rank(int32_t o, int32_t L) {
     return (int32_t)((inv * (int64_t)o) % L);
 }
 
+// Also the symmetry check of the HOGWILD modes: the reverse (j, i) of every
+// owned edge must exist (else kAsymmetric), and the caller compares the
+// number of owned edges with nnz / 2 -- reversal maps the owned edges one-to-
+// one into the others (rows hold no duplicates), so equal counts mean every
+// edge has its reverse.  Entries are written only below `capacity` (the
+// count is checked after the pass).
 __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                       const int32_t *__restrict__ seg_row, const int32_t *__restrict__ deg,
                                       int64_t nnz, int32_t seg_len, const int32_t *__restrict__ pos,
-                                      int4 *__restrict__ ent) {
+                                      int4 *__restrict__ ent, int64_t capacity, uint32_t *flags_out) {
+    uint32_t flags = 0;
     for_each_edge(row_ptr, col_idx, seg_row, nnz, seg_len, [&](int64_t e, int32_t i, int32_t j) {
         if (!ranks_higher(deg[i], deg[j], i, j)) return;
         const int32_t start = pos[row_ptr[i]];
         const int32_t p = start + row_position(pos[e] - start, pos[row_ptr[i + 1]] - start);
         // index of the reverse copy (j, i): binary search for i in row j
-        int64_t lo = row_ptr[j], hi = row_ptr[j + 1] - 1;
+        const int64_t rb = row_ptr[j], re = row_ptr[j + 1];
+        int64_t lo = rb, hi = re - 1;
         while (lo < hi) {
             const int64_t mid = lo + (hi - lo) / 2;
             if (col_idx[mid] < i)
@@ -196,8 +233,13 @@ __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const
             else
                 hi = mid;
         }
-        ent[p] = make_entry(i, j, e, lo);
+        if (lo >= re || col_idx[lo] != i) {
+            flags |= kAsymmetric;
+            return;
+        }
+        if ((int64_t)p >= 0 && (int64_t)p < capacity) ent[p] = make_entry(i, j, e, lo);
     });
+    if (flags) atomicOr(flags_out, flags);
 }
 
 // Chunks of T entries that each vertex's oriented row spans (0: empty row).
@@ -490,13 +532,19 @@ cudaError_t launch_degrees(const int64_t *row_ptr, int32_t n, int32_t *deg, cuda
 
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s,
-                                const int32_t *node_graph) {
-    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
-    if (num_segs <= 0) return cudaSuccess;
+                                const int32_t *node_graph, unsigned long long *upper_count) {
     const int block = 256;
+    {
+        const int64_t want = ((int64_t)n + block - 1) / block;
+        const int grid = (int)(want < 65536 ? (want > 0 ? want : 1) : 65536);
+        check_row_ptr_kernel<<<grid, block, 0, s>>>(row_ptr, n, nnz, flags);
+    }
+    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
+    if (num_segs <= 0) return cudaGetLastError();
     const int64_t want = (num_segs + block - 1) / block;
     const int grid = (int)(want < 65536 ? want : 65536);
-    validate_csr_kernel<<<grid, block, 0, s>>>(row_ptr, col_idx, seg_row, n, nnz, seg_len, flags, node_graph);
+    validate_csr_kernel<<<grid, block, 0, s>>>(row_ptr, col_idx, seg_row, n, nnz, seg_len, flags, node_graph,
+                                               upper_count);
     return cudaGetLastError();
 }
 
@@ -526,10 +574,10 @@ cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in
 
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                   const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  cudaStream_t s) {
+                                  int64_t capacity, uint32_t *flags, cudaStream_t s) {
     const int64_t segs = (nnz + seg_len - 1) / seg_len;
     orient_scatter_kernel<<<grid_for(segs, 256), 256, 0, s>>>(row_ptr, col_idx, seg_row, deg, nnz, seg_len, pos,
-                                                             ent);
+                                                             ent, capacity, flags);
     return cudaGetLastError();
 }
 

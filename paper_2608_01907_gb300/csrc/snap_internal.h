@@ -20,6 +20,7 @@ enum : uint32_t {
     kUnsorted = 4u,       // row not strictly ascending (duplicate or unsorted)
     kAsymmetric = 8u,     // (i, j) present but (j, i) missing
     kCrossGraph = 16u,    // an edge joins two graphs of a batch
+    kBadRowPtr = 32u,     // row_ptr decreases or leaves [0, nnz]
 };
 
 // t-FDP constants (Section 3.1: alpha = 0.1, beta = 8, gamma = 2).
@@ -186,8 +187,8 @@ cudaError_t launch_degrees(const int64_t *row_ptr, int32_t n, int32_t *deg, cuda
 cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, int32_t seg_len,
                                 int32_t *seg_row, int64_t num_segs, cudaStream_t s);
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags,
-                                cudaStream_t s, const int32_t *node_graph = nullptr);
+                                int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s,
+                                const int32_t *node_graph, unsigned long long *upper_count);
 // Construction of the oriented bundle list (flags, exclusive scan, scatter, offsets).
 cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 const int32_t *deg, int64_t nnz, int32_t seg_len, int32_t *flags, cudaStream_t s);
@@ -195,7 +196,7 @@ cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in
                                cudaStream_t s);
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                   const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  cudaStream_t s);
+                                  int64_t capacity, uint32_t *flags, cudaStream_t s);
 // pieces[v] = chunks of T entries that v's oriented row spans.
 cudaError_t launch_row_pieces(const int64_t *act_rp, int32_t n, int32_t T, int32_t *pieces, cudaStream_t s);
 cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,

@@ -178,24 +178,42 @@ def _expect(status, fn, *a, **kw):
     return str(ei.value)
 
 
-def test_create_rejects_malformed_csr(cuda):
+@pytest.mark.parametrize("mode", [snap.MODE_HOGWILD_RED, snap.MODE_HOGWILD, snap.MODE_SYNC])
+def test_create_rejects_malformed_csr(cuda, mode):
+    """Symmetry is checked by the orientation pass (HOGWILD modes) or by the
+    validation pass on half of the edges plus a count (SYNC): both must catch
+    a missing reverse, an extra edge (odd count) and a reverse swapped for
+    another edge (counts still equal)."""
+    o = snap.make_options(mode=mode)
+    create = lambda rp, ci: snap.snap_layout_create(rp, ci, None, len(rp) - 1, o)
     rp, ci = edges_to_csr(4, np.array([0, 1, 2]), np.array([1, 2, 3]))   # path 0-1-2-3
     assert list(ci) == [1, 0, 2, 1, 3, 2]
-    snap.snap_layout_destroy(snap.snap_layout_create(rp, ci))
+    snap.snap_layout_destroy(create(rp, ci))
     bad = ci.copy()
     bad[0] = 0                                           # self-loop at row 0
-    assert "self-loop" in _expect(1, snap.snap_layout_create, rp, bad)
+    assert "self-loop" in _expect(1, create, rp, bad)
     bad = ci.copy()
     bad[1], bad[2] = bad[2], bad[1]                      # row 1 = (2, 0): unsorted
-    assert "ascending" in _expect(1, snap.snap_layout_create, rp, bad)
+    assert "ascending" in _expect(1, create, rp, bad)
     bad = ci.copy()
     bad[-1] = 9                                          # out of range
-    assert "outside" in _expect(1, snap.snap_layout_create, rp, bad)
+    assert "outside" in _expect(1, create, rp, bad)
     asym = ci.copy()
     asym[-1] = 1                                         # (3, 1) without (1, 3)
-    assert "symmetric" in _expect(1, snap.snap_layout_create, rp, asym)
+    assert "symmetric" in _expect(1, create, rp, asym)
+    asym = ci.copy()
+    asym[-1] = 0                                         # (3, 0) instead of (3, 2): a reverse of neither
+    assert "symmetric" in _expect(1, create, rp, asym)
+    odd_rp = np.array([0, 1, 3, 5, 7], np.int64)          # (3, 0) added: 7 directed edges
+    assert "symmetric" in _expect(1, create, odd_rp, np.array([1, 0, 2, 1, 3, 0, 2], np.int32))
+    one_way = np.array([0, 2, 3, 3], np.int64)            # (0, 2) without (2, 0); row 2 empty
+    assert "symmetric" in _expect(1, create, one_way, np.array([1, 2, 0], np.int32))
     dup_rp = np.array([0, 2, 3, 4], np.int64)             # row 0 = (1, 1): duplicate
-    assert "ascending" in _expect(1, snap.snap_layout_create, dup_rp, np.array([1, 1, 0, 0], np.int32))
+    assert "ascending" in _expect(1, create, dup_rp, np.array([1, 1, 0, 0], np.int32))
+    dec_rp = np.array([0, 3, 1, 5, 6], np.int64)          # row_ptr decreases, ends at nnz
+    assert "row_ptr" in _expect(1, create, dec_rp, ci)
+    big_rp = np.array([0, 1, 9, 5, 6], np.int64)          # an offset past nnz
+    assert "row_ptr" in _expect(1, create, big_rp, ci)
 
 
 def test_status_reports_non_finite_positions(cuda):
