@@ -371,8 +371,34 @@ snap_status snap_layout_neighborhood_preservation(snap_layout_t h, const float *
  * synchronise: the memory is freed stream-ordered after the work of the
  * handle's latest call (all work on a handle is assumed to be ordered on the
  * stream of its latest call).  The handle's memory is allocated
- * stream-ordered on the stream given to create. */
+ * stream-ordered on the stream given to create, from a memory pool of the
+ * library's own on that device, which keeps freed memory for the next
+ * handle (snap_memory_cached, snap_memory_trim). */
 void snap_layout_destroy(snap_layout_t h);
+
+/*
+ * snap_memory_cached -- device memory that the library's pool on `device`
+ * holds for reuse: freed by released handles and not given back yet.  A
+ * later create or temporary allocation of the library takes it before it
+ * maps new memory; other allocators do not see it as free
+ * (cudaMemGetInfo counts it as used).  Implementation choice, no
+ * counterpart in the paper: mapping device memory costs about as much as
+ * the rest of a create on a graph of millions of edges.
+ *
+ *   device   CUDA device ordinal (>= 0).
+ *   bytes    host; receives the count (0 if the library has not allocated
+ *            on that device).
+ *
+ * Errors: INVALID_ARG (NULL bytes, device < 0), CUDA.
+ */
+snap_status snap_memory_cached(int32_t device, uint64_t *bytes);
+
+/*
+ * snap_memory_trim -- give the cached memory of the library's pool on
+ * `device` back to the device, down to keep_bytes (0: all of it).  Memory of
+ * live handles is never released.  Errors: INVALID_ARG (device < 0), CUDA.
+ */
+snap_status snap_memory_trim(int32_t device, uint64_t keep_bytes);
 
 /*
  * snap_sampler_table -- the alias table of a weighted sampler for one graph

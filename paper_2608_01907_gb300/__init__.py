@@ -20,7 +20,8 @@ __all__ = [
     "SnapError", "SnapOptions", "SnapSchedule", "MODE_HOGWILD", "MODE_HOGWILD_RED", "MODE_SYNC",
     "SAMPLER_UNIFORM", "SAMPLER_DEGREE", "SAMPLER_WEIGHTS", "build", "library_path", "load_library",
     "snap_options_default", "snap_layout_create", "snap_layout_epochs", "snap_layout_objective",
-    "snap_layout_check", "snap_layout_device_bytes", "snap_layout_destroy", "snap_graph_reorder",
+    "snap_layout_check", "snap_layout_device_bytes", "snap_memory_cached", "snap_memory_trim",
+    "snap_layout_destroy", "snap_graph_reorder",
     "snap_layout_run", "snap_last_error", "Layout", "linear_schedule", "snap_sync_epochs_noalloc",
     "snap_layout_create_batch", "batch_union", "snap_layout_autotune", "MultiEpoch", "snap_sampler_table",
     "snap_layout_epochs_energy", "snap_layout_sync_chunks", "snap_layout_neighborhood_preservation",
@@ -105,6 +106,10 @@ def load_library():
     lib.snap_layout_autotune.restype = st
     lib.snap_layout_device_bytes.argtypes = [P]
     lib.snap_layout_device_bytes.restype = i64
+    lib.snap_memory_cached.argtypes = [i32, P]
+    lib.snap_memory_cached.restype = st
+    lib.snap_memory_trim.argtypes = [i32, u64]
+    lib.snap_memory_trim.restype = st
     lib.snap_layout_destroy.argtypes = [P]
     lib.snap_layout_destroy.restype = None
     lib.snap_sampler_table.argtypes = [i32, P, P, i32, P, P]
@@ -288,6 +293,18 @@ def snap_layout_neighborhood_preservation(h, positions, nodes, stream=None):
 
 def snap_layout_device_bytes(h) -> int:
     return int(load_library().snap_layout_device_bytes(h))
+
+
+def snap_memory_cached(device: int = 0) -> int:
+    """Device bytes the library's memory pool on `device` holds for reuse."""
+    out = ctypes.c_uint64()
+    _check(load_library().snap_memory_cached(device, ctypes.byref(out)))
+    return int(out.value)
+
+
+def snap_memory_trim(device: int = 0, keep_bytes: int = 0) -> None:
+    """Give the pool's cached memory on `device` back, down to keep_bytes."""
+    _check(load_library().snap_memory_trim(device, keep_bytes))
 
 
 def snap_layout_destroy(h) -> None:

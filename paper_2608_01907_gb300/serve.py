@@ -30,7 +30,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (MODE_HOGWILD_RED, MultiEpoch, SnapSchedule, linear_schedule, make_options, snap_layout_create,
-               snap_layout_destroy, snap_layout_device_bytes)
+               snap_layout_destroy, snap_layout_device_bytes, snap_memory_cached)
 
 
 def estimated_bytes(n: int, nnz: int) -> int:
@@ -134,7 +134,8 @@ class LayoutServer:
         torch = self.torch
         if not self.waiting or len(self.active) >= self.max_jobs:
             return
-        free = torch.cuda.mem_get_info()[0] - FREE_MARGIN
+        # free device memory, plus what the library's pool holds for reuse
+        free = torch.cuda.mem_get_info()[0] + snap_memory_cached(torch.cuda.current_device()) - FREE_MARGIN
         while self.waiting and len(self.active) < self.max_jobs:
             job = self.waiting[0]
             need = estimated_bytes(job.n, job.nnz)

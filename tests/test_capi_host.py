@@ -152,6 +152,10 @@ def test_null_handle_errors(lib):
     P = ctypes.c_void_p
     assert lib.snap_layout_check(None, None) == 1
     assert lib.snap_layout_device_bytes(None) == 0
+    out = ctypes.c_uint64(7)
+    assert lib.snap_memory_cached(0, None) == 1 and lib.snap_memory_cached(-1, ctypes.byref(out)) == 1
+    assert lib.snap_memory_cached(0, ctypes.byref(out)) == 0 and out.value == 0   # nothing allocated here
+    assert lib.snap_memory_trim(-1, 0) == 1 and lib.snap_memory_trim(0, 0) == 0
     lib.snap_layout_destroy(None)
     sched = snap.linear_schedule()
     assert lib.snap_layout_epochs(None, P(8), 0, 1, 3, ctypes.byref(sched), 1, None) == 1

@@ -231,17 +231,44 @@ def test_status_reports_non_finite_positions(cuda):
 def test_injected_allocation_failure_leaks_nothing(cuda, monkeypatch):
     torch = cuda
     g = tiny_graph(1000, 3000, seed=5)
+    dev = torch.cuda.current_device()
     torch.cuda.synchronize()
-    free0 = torch.cuda.mem_get_info()[0]
+    # free device memory plus what the library's pool keeps for reuse
+    free0 = torch.cuda.mem_get_info()[0] + snap.snap_memory_cached(dev)
     for nth in (1, 2, 3, 5):
         monkeypatch.setenv("SNAP_FAULT_INJECT", f"alloc:{nth}")
         _expect(2, snap.snap_layout_create, g.row_ptr, g.col_idx,
                 opts=snap.make_options(mode=snap.MODE_SYNC))
     monkeypatch.delenv("SNAP_FAULT_INJECT")
     torch.cuda.synchronize()
-    assert abs(torch.cuda.mem_get_info()[0] - free0) < (4 << 20)
+    assert abs(torch.cuda.mem_get_info()[0] + snap.snap_memory_cached(dev) - free0) < (4 << 20)
     h = snap.snap_layout_create(g.row_ptr, g.col_idx)
     snap.snap_layout_destroy(h)
+
+
+def test_memory_pool_keeps_and_trims(cuda):
+    """A destroyed handle's memory stays in the library's pool (counted by
+    snap_memory_cached, reused by the next create) until snap_memory_trim."""
+    torch = cuda
+    dev = torch.cuda.current_device()
+    g = tiny_graph(20000, 100000, seed=3)
+    h = snap.snap_layout_create(g.row_ptr, g.col_idx)
+    held = snap.snap_layout_device_bytes(h)
+    snap.snap_layout_destroy(h)
+    torch.cuda.synchronize()
+    cached = snap.snap_memory_cached(dev)
+    assert cached >= held
+    free_cached = torch.cuda.mem_get_info()[0]
+    h = snap.snap_layout_create(g.row_ptr, g.col_idx)        # served from the cache
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free_cached - (4 << 20)
+    assert snap.snap_memory_cached(dev) < cached
+    snap.snap_layout_destroy(h)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    snap.snap_memory_trim(dev, 0)
+    assert snap.snap_memory_cached(dev) == 0
+    assert torch.cuda.mem_get_info()[0] >= free_before + held - (4 << 20)
 
 
 def test_run_from_host_buffers_matches_device_path(cuda):
