@@ -228,6 +228,7 @@ struct snap_layout {
     int2 *d_act_meta = nullptr;
     int64_t act_ent_bytes = 0, act_meta_bytes = 0;
     int32_t *d_act_pieces = nullptr;      // chunks each vertex's oriented row spans
+    int32_t *d_orient = nullptr;          // during create: orientation flags from the validation pass
     int64_t act_pieces_bytes = 0;
     // batch of graphs (num_graphs > 1): graph of every vertex and per-graph table
     int32_t num_graphs = 1;
@@ -288,6 +289,8 @@ struct snap_layout {
 
     void release() {
         release_csr();
+        free_async(d_orient);
+        d_orient = nullptr;
         free_async(d_act_row_ptr);
         free_async(d_act_ent);
         free_async(d_act_meta);
@@ -353,15 +356,37 @@ static int64_t golden_multiplier(int64_t m) {
 // (Re)cuts the oriented list into chunks of `target` entries: the entries
 // move from the current layout (row-major right after construction) into a
 // fresh array in the new slot order, and the slot table is rebuilt.
-static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, int32_t order, cudaStream_t stream) {
-    if (h->act_nnz > 0 && target > h->act_nnz) target = (int32_t)h->act_nnz;   // one chunk
-    if (h->last_use) cudaStreamWaitEvent(stream, h->last_use, 0);   // the old arrays' last readers
+// The chunked layout of `entries` oriented entries in chunks of `target`
+// (at most one chunk's worth of entries) in row order `order`.
+static ChunkLayout make_chunk_layout(int64_t entries, int32_t target, int32_t order) {
+    if (entries > 0 && target > entries) target = (int32_t)entries;   // one chunk
     ChunkLayout to;
     to.T = target;
     to.order = order;
-    to.S = (h->act_nnz + target - 1) / target;
+    to.S = (entries + target - 1) / target;
     to.mul = golden_multiplier(to.S);
     to.add = to.S > 1 ? to.S / 3 : 0;
+    return to;
+}
+
+// Makes (ent, meta) in layout `to` the handle's oriented list.
+static void install_chunks(snap_layout *h, int4 *ent, int2 *meta, const ChunkLayout &to, int64_t ent_bytes,
+                           int64_t meta_bytes) {
+    h->device_bytes += ent_bytes + meta_bytes - h->act_ent_bytes - h->act_meta_bytes;
+    h->d_act_ent = ent;
+    h->d_act_meta = meta;
+    h->act_ent_bytes = ent_bytes;
+    h->act_meta_bytes = meta_bytes;
+    h->act_layout = to;
+    h->act_seg_len = to.T;
+    h->act_num_segs = to.S;
+    h->perm_mul = golden_multiplier((to.S + 31) / 32);
+}
+
+static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, int32_t order, cudaStream_t stream) {
+    if (h->last_use) cudaStreamWaitEvent(stream, h->last_use, 0);   // the old arrays' last readers
+    const ChunkLayout to = make_chunk_layout(h->act_nnz, target, order);
+    target = to.T;
     const int64_t ent_bytes = (int64_t)sizeof(int4) * (to.S > 0 ? to.S * (int64_t)target : 1);
     const int64_t meta_bytes = (int64_t)sizeof(int2) * (to.S > 0 ? to.S : 1);
     int4 *ent = nullptr;
@@ -395,20 +420,14 @@ static cudaError_t set_chunks(snap_layout *h, AllocCounter &ac, int32_t target, 
     }
     cudaFreeAsync(h->d_act_ent, stream);
     if (h->d_act_meta) cudaFreeAsync(h->d_act_meta, stream);
-    h->device_bytes += ent_bytes + meta_bytes - h->act_ent_bytes - h->act_meta_bytes;
-    h->d_act_ent = ent;
-    h->d_act_meta = meta;
-    h->act_ent_bytes = ent_bytes;
-    h->act_meta_bytes = meta_bytes;
-    h->act_layout = to;
-    h->act_seg_len = target;
-    h->act_num_segs = to.S;
-    h->perm_mul = golden_multiplier((to.S + 31) / 32);
+    install_chunks(h, ent, meta, to, ent_bytes, meta_bytes);
     return cudaSuccess;
 }
 
 // Builds the oriented bundle list from the validated device CSR and then
 // frees the CSR (the HOGWILD kernels and the objective need only the list).
+// The oriented list of a validated CSR.  h->d_orient holds the orientation
+// flags the validation pass wrote (nnz + 1 entries); it is consumed here.
 static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t stream) {
     const int32_t n = h->n;
     const int64_t nnz = h->nnz;
@@ -421,7 +440,14 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
         // 128).  Concurrency is bounded separately (max_inflight).
         h->act_seg_len = 4;
     }
-    int32_t *flags = nullptr, *pos = nullptr;
+    const ChunkLayout to = make_chunk_layout(h->act_nnz, h->act_seg_len,
+                                             (h->opts.flags & SNAP_FLAG_ASCENDING_ROWS) ? 1 : 0);
+    const int64_t ent_bytes = (int64_t)sizeof(int4) * (to.S > 0 ? to.S * (int64_t)to.T : 1);
+    const int64_t meta_bytes = (int64_t)sizeof(int2) * (to.S > 0 ? to.S : 1);
+    const int64_t pieces_bytes = (int64_t)sizeof(int32_t) * (n > 0 ? n : 1);
+    int32_t *pos = nullptr;
+    int4 *ent = nullptr;
+    int2 *meta = nullptr;
     void *temp = nullptr;
     size_t temp_bytes = 0;
     cudaError_t err = cudaSuccess;
@@ -442,20 +468,21 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
         }
     };
     alloc((void **)&h->d_act_row_ptr, sizeof(int64_t) * ((size_t)n + 1), true, "oriented row offsets");
-    alloc((void **)&h->d_act_ent, sizeof(int4) * (size_t)(h->act_nnz > 0 ? h->act_nnz : 1), false,
-          "oriented entries");
-    alloc((void **)&flags, sizeof(int32_t) * ((size_t)nnz + 1), false, "orientation flags");
+    alloc((void **)&ent, (size_t)ent_bytes, false, "oriented entries");
+    alloc((void **)&meta, (size_t)meta_bytes, false, "slot descriptors");
+    alloc((void **)&h->d_act_pieces, (size_t)pieces_bytes, true, "row pieces");
     alloc((void **)&pos, sizeof(int32_t) * ((size_t)nnz + 1), false, "orientation offsets");
-    if (err == cudaSuccess) step(exclusive_scan_i32(nullptr, &temp_bytes, flags, pos, nnz + 1, stream), "scan size");
+    if (err == cudaSuccess)
+        step(exclusive_scan_i32(nullptr, &temp_bytes, h->d_orient, pos, nnz + 1, stream), "scan size");
     alloc(&temp, temp_bytes, false, "scan scratch");
     if (err == cudaSuccess) {
-        step(launch_orient_flags(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, flags, stream),
-             "orientation flags kernel");
-        step(exclusive_scan_i32(temp, &temp_bytes, flags, pos, nnz + 1, stream), "orientation scan");
-        step(launch_orient_scatter(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, pos,
-                                   h->d_act_ent, h->act_nnz, h->d_status + 1, stream),
+        h->act_pieces_bytes = pieces_bytes;
+        step(exclusive_scan_i32(temp, &temp_bytes, h->d_orient, pos, nnz + 1, stream), "orientation scan");
+        step(launch_orient_scatter(h->d_row_ptr, h->d_col, h->d_seg_row, h->d_deg, nnz, h->seg_len, pos, to, ent,
+                                   meta, h->act_nnz, h->d_status + 1, stream),
              "orientation scatter kernel");
         step(launch_orient_rowptr(h->d_row_ptr, pos, n, h->d_act_row_ptr, stream), "orientation offsets kernel");
+        step(launch_row_pieces(h->d_act_row_ptr, n, to.T, h->d_act_pieces, stream), "row pieces kernel");
     }
     int64_t total = -1;
     if (err == cudaSuccess) {
@@ -465,18 +492,21 @@ static snap_status build_oriented(snap_layout *h, AllocCounter &ac, cudaStream_t
              "read symmetry word");
         step(cudaStreamSynchronize(stream), "orientation");
     }
-    if (flags) cudaFreeAsync(flags, stream);
+    cudaFreeAsync(h->d_orient, stream);
+    h->d_orient = nullptr;
     if (pos) cudaFreeAsync(pos, stream);
     if (temp) cudaFreeAsync(temp, stream);
-    if (err != cudaSuccess) return cuda_fail(err, what);
+    if (err != cudaSuccess) {
+        if (ent) cudaFreeAsync(ent, stream);
+        if (meta) cudaFreeAsync(meta, stream);
+        return cuda_fail(err, what);
+    }
+    h->act_ent_bytes = 0;
+    h->act_meta_bytes = 0;
+    install_chunks(h, ent, meta, to, ent_bytes, meta_bytes);
     // every owned edge has its reverse and half of the edges are owned: symmetric
     if ((h->h_status[1] & kAsymmetric) || (nnz & 1) || total != h->act_nnz)
         return fail(SNAP_ERR_INVALID_ARG, "the CSR is not symmetric: some (i, j) has no (j, i)");
-    h->act_layout = ChunkLayout{0, 0, 0, 0};   // row-major, rows in the affine order of the scatter
-    h->act_ent_bytes = 0;
-    err = set_chunks(h, ac, h->act_seg_len, (h->opts.flags & SNAP_FLAG_ASCENDING_ROWS) ? 1 : 0, stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
-    if (err != cudaSuccess) return cuda_fail(err, "oriented chunks");
     if (!(h->opts.flags & SNAP_FLAG_KEEP_CSR)) {
         h->device_bytes -= (int64_t)(sizeof(int64_t) * ((size_t)n + 1) +
                                      sizeof(int32_t) * (size_t)(h->num_segs * h->seg_len + 4) +
@@ -708,12 +738,22 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     }
     SNAP_CUDA(launch_segment_rows(h->d_row_ptr, n, h->nnz, h->seg_len, h->d_seg_row, h->num_segs, stream),
               "segment table kernel");
-    // symmetry: here for the synchronous mode, in the orientation pass otherwise
+    // symmetry: here for the synchronous mode, in the orientation pass otherwise;
+    // the HOGWILD modes also take the orientation flags from this pass
     unsigned long long *upper = o.mode == SNAP_MODE_SYNC
                                     ? reinterpret_cast<unsigned long long *>(h->d_status + 2)
                                     : nullptr;
+    if (o.mode != SNAP_MODE_SYNC && h->nnz > 0) {
+        err = dev_alloc(ac, (void **)&h->d_orient, sizeof(int32_t) * ((size_t)h->nnz + 1), stream);
+        if (err != cudaSuccess) {
+            h->release();
+            delete h;
+            cudaGetLastError();
+            return cuda_fail(err, "device allocation of the orientation flags");
+        }
+    }
     SNAP_CUDA(launch_validate_csr(h->d_row_ptr, h->d_col, h->d_seg_row, n, h->nnz, h->seg_len, h->d_status + 1,
-                                  stream, h->d_node_graph, upper), "validation kernel");
+                                  stream, h->d_node_graph, upper, h->d_deg, h->d_orient), "validation kernel");
     SNAP_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, stream),
               "read validation word");
     SNAP_CUDA(cudaStreamSynchronize(stream), "create");

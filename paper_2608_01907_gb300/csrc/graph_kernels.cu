@@ -39,6 +39,14 @@ __global__ void degrees_kernel(const int64_t *__restrict__ row_ptr, int32_t n, i
         deg[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
 }
 
+// Orientation of the undirected edges: {i, j} belongs to the bundle of the
+// endpoint that ranks higher by (degree, then smaller id).  That endpoint's
+// lane processes both directed copies (i, j) and (j, i), so a vertex is a
+// partner only of its higher-ranked neighbours.
+__device__ __forceinline__ bool ranks_higher(int32_t di, int32_t dj, int32_t i, int32_t j) {
+    return di > dj || (di == dj && i < j);
+}
+
 // row_ptr non-decreasing inside [0, nnz] (row_ptr[0] = 0 and row_ptr[n] =
 // nnz are checked on the host).  Every kernel that runs before this result
 // is read clamps the offsets it uses as indices.
@@ -61,10 +69,15 @@ __global__ void check_row_ptr_kernel(const int64_t *__restrict__ row_ptr, int32_
 // them one-to-one into the edges with j > i, so equal counts mean every edge
 // has its reverse.  (The HOGWILD modes check symmetry the same way in the
 // orientation pass, which searches the reverse of half of the edges anyway.)
+// orient != null (the HOGWILD modes): also orient[e] = 1 when edge e's
+// source ranks higher than its partner (ranks_higher; deg = row lengths),
+// else 0, and orient[nnz] = 0 -- the input of the orientation scan.
 __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                     const int32_t *__restrict__ seg_row, int32_t n, int64_t nnz,
                                     int32_t seg_len, uint32_t *flags_out, const int32_t *__restrict__ node_graph,
-                                    unsigned long long *upper_count) {
+                                    unsigned long long *upper_count, const int32_t *__restrict__ deg,
+                                    int32_t *__restrict__ orient) {
+    if (orient && blockIdx.x == 0 && threadIdx.x == 0) orient[nnz] = 0;
     const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t flags = 0;
@@ -84,8 +97,10 @@ __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const i
             const int32_t j = col_idx[e];
             if (j < 0 || j >= n) {
                 flags |= kBadColumn;
+                if (orient) orient[e] = 0;
                 continue;
             }
+            if (orient) orient[e] = ranks_higher(deg[row], deg[j], row, j) ? 1 : 0;
             if (j == row) flags |= kSelfLoop;
             if (node_graph && node_graph[j] != node_graph[row]) flags |= kCrossGraph;
             if (e > row_begin && e > 0 && col_idx[e - 1] >= j) flags |= kUnsorted;
@@ -114,44 +129,7 @@ __global__ void validate_csr_kernel(const int64_t *__restrict__ row_ptr, const i
     if (upper_count && upper) atomicAdd(upper_count, upper);
 }
 
-// Orientation of the undirected edges: {i, j} belongs to the bundle of the
-// endpoint that ranks higher by (degree, then smaller id).  That endpoint's
-// lane processes both directed copies (i, j) and (j, i), so a vertex is a
-// partner only of its higher-ranked neighbours.
-__device__ __forceinline__ bool ranks_higher(int32_t di, int32_t dj, int32_t i, int32_t j) {
-    return di > dj || (di == dj && i < j);
-}
 
-// Walks the CSR segment by segment and calls body(e, row, col) per edge.
-template <typename Body>
-__device__ __forceinline__ void for_each_edge(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                                              const int32_t *__restrict__ seg_row, int64_t nnz, int32_t seg_len,
-                                              Body body) {
-    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
-        const int64_t e0 = s * seg_len;
-        const int64_t e1 = min(e0 + (int64_t)seg_len, nnz);
-        int32_t row = seg_row[s];
-        int64_t row_end = row_ptr[row + 1];
-        for (int64_t e = e0; e < e1; ++e) {
-            while (e >= row_end) {
-                ++row;
-                row_end = row_ptr[row + 1];
-            }
-            body(e, row, col_idx[e]);
-        }
-    }
-}
-
-__global__ void orient_flags_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                                    const int32_t *__restrict__ seg_row, const int32_t *__restrict__ deg,
-                                    int64_t nnz, int32_t seg_len, int32_t *__restrict__ flags) {
-    for_each_edge(row_ptr, col_idx, seg_row, nnz, seg_len, [&](int64_t e, int32_t i, int32_t j) {
-        flags[e] = ranks_higher(deg[i], deg[j], i, j) ? 1 : 0;
-    });
-    if (blockIdx.x == 0 && threadIdx.x == 0) flags[nnz] = 0;
-}
 
 // Entry of an oriented edge {i, j}: {j, index of (i, j), index of (j, i), i}
 // -- the CSR indices of both directed copies (a handle holds fewer than 2^32
@@ -208,37 +186,85 @@ __device__ __forceinline__ int32_t row_rank(int32_t o, int32_t L) {
     return (int32_t)((inv * (int64_t)o) % L);
 }
 
+// Builds the oriented list directly in its chunked, slot-interleaved layout
+// `to` (both row orders): owned edge e of row i has rank r = pos[e] -
+// pos[row_ptr[i]] among its row's owned edges (ascending partner id), sits at
+// row position r (ascending order) or (a r) mod L (affine order,
+// row_position), hence at list index pt = pos[row_ptr[i]] + that, in chunk
+// pt / T; the entry is written to its slot's place and the chunk's first
+// entry writes the slot descriptor {i, chunk}.  Along a row the ranks of
+// consecutive owned edges go up by one, so the affine position advances by
+// a mod L, and a = row_multiplier(L) is found once per row run.
 // Also the symmetry check of the HOGWILD modes: the reverse (j, i) of every
 // owned edge must exist (else kAsymmetric), and the caller compares the
 // number of owned edges with nnz / 2 -- reversal maps the owned edges one-to-
 // one into the others (rows hold no duplicates), so equal counts mean every
-// edge has its reverse.  Entries are written only below `capacity` (the
+// edge has its reverse.  Entries are written only for pt < capacity (the
 // count is checked after the pass).
 __global__ void orient_scatter_kernel(const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                                       const int32_t *__restrict__ seg_row, const int32_t *__restrict__ deg,
                                       int64_t nnz, int32_t seg_len, const int32_t *__restrict__ pos,
-                                      int4 *__restrict__ ent, int64_t capacity, uint32_t *flags_out) {
+                                      const ChunkLayout to, int4 *__restrict__ ent, int2 *__restrict__ meta,
+                                      int64_t capacity, uint32_t *flags_out) {
     uint32_t flags = 0;
-    for_each_edge(row_ptr, col_idx, seg_row, nnz, seg_len, [&](int64_t e, int32_t i, int32_t j) {
-        if (!ranks_higher(deg[i], deg[j], i, j)) return;
-        const int32_t start = pos[row_ptr[i]];
-        const int32_t p = start + row_position(pos[e] - start, pos[row_ptr[i + 1]] - start);
-        // index of the reverse copy (j, i): binary search for i in row j
-        const int64_t rb = row_ptr[j], re = row_ptr[j + 1];
-        int64_t lo = rb, hi = re - 1;
-        while (lo < hi) {
-            const int64_t mid = lo + (hi - lo) / 2;
-            if (col_idx[mid] < i)
-                lo = mid + 1;
-            else
-                hi = mid;
+    const int64_t num_segs = (nnz + seg_len - 1) / seg_len;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < num_segs; s += stride) {
+        const int64_t e0 = s * seg_len;
+        const int64_t e1 = min(e0 + (int64_t)seg_len, nnz);
+        int32_t i = seg_row[s];
+        int64_t row_end = row_ptr[i + 1];
+        int32_t run_row = -1, L = 0, a = 1, last_r = -2, last_o = 0;
+        int64_t start = 0;
+        for (int64_t e = e0; e < e1; ++e) {
+            while (e >= row_end) {
+                ++i;
+                row_end = row_ptr[i + 1];
+            }
+            const int32_t j = col_idx[e];
+            if (!ranks_higher(deg[i], deg[j], i, j)) continue;
+            if (i != run_row) {
+                run_row = i;
+                start = pos[row_ptr[i]];
+                L = (int32_t)(pos[row_end] - start);
+                a = L > 2 ? (int32_t)row_multiplier(L) : 1;
+                last_r = -2;
+            }
+            const int32_t r = (int32_t)(pos[e] - start);
+            int32_t o = r;
+            if (to.order == 0 && L > 2) {
+                if (r == last_r + 1) {
+                    o = last_o + a;
+                    if (o >= L) o -= L;
+                } else {
+                    o = (int32_t)(((int64_t)a * r) % L);
+                }
+            }
+            last_r = r;
+            last_o = o;
+            // index of the reverse copy (j, i): binary search for i in row j
+            const int64_t rb = row_ptr[j], re = row_ptr[j + 1];
+            int64_t lo = rb, hi = re - 1;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (col_idx[mid] < i)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo >= re || col_idx[lo] != i) {
+                flags |= kAsymmetric;
+                continue;
+            }
+            const int64_t pt = start + o;
+            if (pt < 0 || pt >= capacity) continue;
+            const int64_t c = pt / to.T;
+            const int64_t t = pt - c * to.T;
+            const int64_t slot = chunk_slot(to, c);
+            ent[chunk_entry_index(slot, to.S, to.T, t)] = make_entry(i, j, e, lo);
+            if (t == 0) meta[slot] = make_int2(i, (int32_t)c);
         }
-        if (lo >= re || col_idx[lo] != i) {
-            flags |= kAsymmetric;
-            return;
-        }
-        if ((int64_t)p >= 0 && (int64_t)p < capacity) ent[p] = make_entry(i, j, e, lo);
-    });
+    }
     if (flags) atomicOr(flags_out, flags);
 }
 
@@ -275,21 +301,10 @@ __global__ void chunk_layout_kernel(const int4 *__restrict__ src, const ChunkLay
         }
         // p is the entry's row-major index in `from`'s row order; pt its index
         // in `to`'s (the same row, another place when the orders differ)
+        const int4 en = src[q];
         int64_t pt = p;
-        int32_t row = -1;
-        auto row_of = [&](int64_t x) {
-            int32_t lo = 0, hi = n - 1;   // last row starting at or before x: the row holding x
-            while (lo < hi) {
-                const int32_t mid = lo + (hi - lo + 1) / 2;
-                if (act_rp[mid] <= x)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            return lo;
-        };
         if (from.order != to.order) {
-            row = row_of(p);
+            const int32_t row = en.w;   // the entry names its row
             const int64_t b = act_rp[row];
             const int32_t L = (int32_t)(act_rp[row + 1] - b), o = (int32_t)(p - b);
             const int32_t rank = from.order == 0 ? row_rank(o, L) : o;
@@ -298,8 +313,8 @@ __global__ void chunk_layout_kernel(const int4 *__restrict__ src, const ChunkLay
         const int64_t c = pt / to.T;
         const int64_t t = pt - c * to.T;
         const int64_t slot = chunk_slot(to, c);
-        dst[chunk_entry_index(slot, to.S, to.T, t)] = src[q];
-        if (t == 0) meta[slot] = make_int2(row >= 0 ? row : row_of(pt), (int32_t)c);
+        dst[chunk_entry_index(slot, to.S, to.T, t)] = en;
+        if (t == 0) meta[slot] = make_int2(en.w, (int32_t)c);
     }
 }
 
@@ -532,7 +547,8 @@ cudaError_t launch_degrees(const int64_t *row_ptr, int32_t n, int32_t *deg, cuda
 
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s,
-                                const int32_t *node_graph, unsigned long long *upper_count) {
+                                const int32_t *node_graph, unsigned long long *upper_count, const int32_t *deg,
+                                int32_t *orient) {
     const int block = 256;
     {
         const int64_t want = ((int64_t)n + block - 1) / block;
@@ -544,7 +560,7 @@ cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, 
     const int64_t want = (num_segs + block - 1) / block;
     const int grid = (int)(want < 65536 ? want : 65536);
     validate_csr_kernel<<<grid, block, 0, s>>>(row_ptr, col_idx, seg_row, n, nnz, seg_len, flags, node_graph,
-                                               upper_count);
+                                               upper_count, deg, orient);
     return cudaGetLastError();
 }
 
@@ -560,12 +576,6 @@ static int grid_for(int64_t items, int block) {
     return (int)(want < 65536 ? (want > 0 ? want : 1) : 65536);
 }
 
-cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                const int32_t *deg, int64_t nnz, int32_t seg_len, int32_t *flags, cudaStream_t s) {
-    const int64_t segs = (nnz + seg_len - 1) / seg_len;
-    orient_flags_kernel<<<grid_for(segs, 256), 256, 0, s>>>(row_ptr, col_idx, seg_row, deg, nnz, seg_len, flags);
-    return cudaGetLastError();
-}
 
 cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in, int32_t *out, int64_t count,
                                cudaStream_t s) {
@@ -573,11 +583,12 @@ cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in
 }
 
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                  const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  int64_t capacity, uint32_t *flags, cudaStream_t s) {
+                                  const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos,
+                                  const ChunkLayout &to, int4 *ent, int2 *meta, int64_t capacity, uint32_t *flags,
+                                  cudaStream_t s) {
     const int64_t segs = (nnz + seg_len - 1) / seg_len;
     orient_scatter_kernel<<<grid_for(segs, 256), 256, 0, s>>>(row_ptr, col_idx, seg_row, deg, nnz, seg_len, pos,
-                                                             ent, capacity, flags);
+                                                             to, ent, meta, capacity, flags);
     return cudaGetLastError();
 }
 

@@ -188,15 +188,17 @@ cudaError_t launch_segment_rows(const int64_t *row_ptr, int32_t n, int64_t nnz, 
                                 int32_t *seg_row, int64_t num_segs, cudaStream_t s);
 cudaError_t launch_validate_csr(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
                                 int32_t n, int64_t nnz, int32_t seg_len, uint32_t *flags, cudaStream_t s,
-                                const int32_t *node_graph, unsigned long long *upper_count);
-// Construction of the oriented bundle list (flags, exclusive scan, scatter, offsets).
-cudaError_t launch_orient_flags(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                const int32_t *deg, int64_t nnz, int32_t seg_len, int32_t *flags, cudaStream_t s);
+                                const int32_t *node_graph, unsigned long long *upper_count, const int32_t *deg,
+                                int32_t *orient);
+// Construction of the oriented bundle list: the flags come from the
+// validation pass (launch_validate_csr's orient), then exclusive scan,
+// scatter into the chunked layout, offsets.
 cudaError_t exclusive_scan_i32(void *temp, size_t *temp_bytes, const int32_t *in, int32_t *out, int64_t count,
                                cudaStream_t s);
 cudaError_t launch_orient_scatter(const int64_t *row_ptr, const int32_t *col_idx, const int32_t *seg_row,
-                                  const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos, int4 *ent,
-                                  int64_t capacity, uint32_t *flags, cudaStream_t s);
+                                  const int32_t *deg, int64_t nnz, int32_t seg_len, const int32_t *pos,
+                                  const ChunkLayout &to, int4 *ent, int2 *meta, int64_t capacity, uint32_t *flags,
+                                  cudaStream_t s);
 // pieces[v] = chunks of T entries that v's oriented row spans.
 cudaError_t launch_row_pieces(const int64_t *act_rp, int32_t n, int32_t T, int32_t *pieces, cudaStream_t s);
 cudaError_t launch_orient_rowptr(const int64_t *row_ptr, const int32_t *pos, int32_t n, int64_t *act_row_ptr,
