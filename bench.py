@@ -509,6 +509,20 @@ def run_snap(args, rank, world, local_rank):
         extras["objective_sampled"] = {"initial": o0, "final": o1}
         extras["device_bytes"] = snap.snap_layout_device_bytes(h)
     snap.snap_layout_destroy(h)
+    if rank == 0 and not args.no_extras and n <= (1 << 25):
+        # NP (Section 4.1, r = 2) of the timed layout on 1,024 seeded non-isolated vertices, on the device
+        # (each sample reads all positions 13 times: skipped above 2^25 vertices)
+        deg_all = np.diff(row_ptr)
+        live = np.flatnonzero(deg_all > 0)
+        nodes = np.random.default_rng(2024).choice(live, min(1024, live.size), replace=False).astype(np.int32)
+        hn = snap.snap_layout_create(row_ptr, col_idx, None, n, snap.make_options(keep_csr=True), stream)
+        t_np = time.perf_counter()
+        np0 = snap.snap_layout_neighborhood_preservation(hn, Y0_d, nodes, stream)[0]
+        np1 = snap.snap_layout_neighborhood_preservation(hn, Y, nodes, stream)[0]
+        t_np = time.perf_counter() - t_np
+        snap.snap_layout_destroy(hn)
+        extras["np_sampled"] = {"initial": np0, "final": np1, "vertices": int(nodes.size),
+                                "seconds_for_both": t_np}
     if rank == 0 and not args.no_extras:
         # the other modes on the same graph, 5 epochs each (not the headline)
         variants = [(f"mode_{m}", c, sampler) for m, c in (("hogwild", snap.MODE_HOGWILD),

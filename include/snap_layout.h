@@ -115,7 +115,7 @@ typedef struct {
                                  modes the length of a chunk of the oriented list (entries of 2
                                  directed edges each; a chunk may span rows, and a graph with at most
                                  this many entries is one chunk, so one lane); in SYNC directed
-                                 edges; 0 = default (HOGWILD: 4; SYNC: 32) */
+                                 edges; 0 = default (HOGWILD: 4; SYNC: 16) */
     int32_t block_threads;    /* threads per block; 0 = default (256) */
     int32_t flags;            /* SNAP_FLAG_* bits */
     float max_inflight;       /* HOGWILD modes: at most this share of the graph's entries in flight at
@@ -358,10 +358,12 @@ snap_status snap_layout_autotune(snap_layout_t h, const float *initial_positions
  *   out_used    host, nullable: the number of those samples.
  *
  * Needs the handle's device CSR: SYNC handles keep it, HOGWILD handles only
- * with SNAP_FLAG_KEEP_CSR (else NOT_SUPPORTED); every graph of the handle has
- * at most 262,144 vertices (else NOT_SUPPORTED).  Allocates small scratch,
- * synchronises the stream.  Errors: INVALID_ARG, NOT_SUPPORTED,
- * OUT_OF_MEMORY, CUDA, NUMERIC (from an earlier call).
+ * with SNAP_FLAG_KEEP_CSR (else NOT_SUPPORTED).  Each sample reads its graph's
+ * positions 13 times (an exact radix select of the k-th nearest).  Allocates
+ * scratch (for graphs above 262,144 vertices a 2-hop bitmap of n bits per
+ * concurrent sample, at most 1 GiB), synchronises the stream.  Errors:
+ * INVALID_ARG, NOT_SUPPORTED, OUT_OF_MEMORY, CUDA, NUMERIC (from an earlier
+ * call).
  */
 snap_status snap_layout_neighborhood_preservation(snap_layout_t h, const float *positions, const int32_t *nodes,
                                                   int32_t count, double *out_mean, int32_t *out_used,
@@ -479,8 +481,8 @@ snap_status snap_layout_run(const int64_t *row_ptr, const int32_t *col_idx, int3
  * reverse present); a violation returns INVALID_ARG with the positions
  * untouched.  A buffer that is not device memory of the current device is
  * INVALID_ARG too.  The result equals snap_layout_epochs on a
- * SNAP_MODE_SYNC handle with the same substeps and cap (default 32-edge
- * segments).  The first call on a device looks up the scratch's device
+ * SNAP_MODE_SYNC handle with the same substeps and cap (with any segment
+ * length: the sums are integer).  The first call on a device looks up the scratch's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls in the process share the scratch, which keeps the last
  * call's contents (each call clears it first): calls that overlap on the GPU

@@ -652,7 +652,11 @@ static snap_status create_impl(const int64_t *row_ptr, const int32_t *col_idx, c
     if (graph_offsets && num_graphs > 1) h->graph_offsets.assign(graph_offsets, graph_offsets + num_graphs + 1);
     // CSR segments: the synchronous kernel's unit of work (and the
     // validation pass); the HOGWILD modes use chunks of oriented entries.
-    h->seg_len = (o.mode == SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 32;
+    // SYNC takes 16 edges by default: a chunk of 1/S of the edges in 32-edge
+    // segments leaves a tail wave (R-MAT 2^22, S = 16: 7.08 ms per epoch at
+    // 32, 6.78 at 16, 6.89 at 8, 7.72 at 4; the sums are integer, so the
+    // result is the same for every length).
+    h->seg_len = o.mode == SNAP_MODE_SYNC ? (o.segment_edges ? o.segment_edges : 16) : 32;
     h->act_seg_len = (o.mode != SNAP_MODE_SYNC && o.segment_edges) ? o.segment_edges : 0;   // 0: by size
     h->block = o.block_threads ? o.block_threads : 256;
     h->num_segs = (h->nnz + h->seg_len - 1) / h->seg_len;
@@ -1304,9 +1308,6 @@ static snap_status np_impl(snap_layout *h, const float2 *pos, const int32_t *nod
         max_graph = 0;
         for (const GraphInfo &gi : h->h_graphs) max_graph = gi.n > max_graph ? gi.n : max_graph;
     }
-    if (max_graph > kNpMaxGraph)
-        return fail(SNAP_ERR_NOT_SUPPORTED, "NP needs graphs of at most %d vertices (largest: %d)", kNpMaxGraph,
-                    max_graph);
     for (int32_t q = 0; q < count; ++q)
         if (nodes[q] < 0 || nodes[q] >= h->n) return fail(SNAP_ERR_INVALID_ARG, "sample %d outside [0, n)", q);
     *mean = 0.0;
@@ -1315,19 +1316,34 @@ static snap_status np_impl(snap_layout *h, const float2 *pos, const int32_t *nod
     AllocCounter ac;
     int32_t *d_nodes = nullptr;
     double *d_out = nullptr;
+    uint32_t *d_bits = nullptr;
+    int grid = h->sms * 8;
+    int64_t words = 0;
     cudaError_t err = dev_alloc(ac, (void **)&d_nodes, sizeof(int32_t) * (size_t)count, stream);
     if (err == cudaSuccess) err = dev_alloc(ac, (void **)&d_out, sizeof(double) * (size_t)count, stream);
+    if (err == cudaSuccess && max_graph > kNpMaxGraph) {
+        // 2-hop bitmaps in global scratch: one row per block, at most 1 GiB in all
+        words = ((int64_t)max_graph + 31) / 32;
+        int64_t g = (int64_t)h->sms * 2;
+        const int64_t cap = ((int64_t)1 << 30) / (words * (int64_t)sizeof(uint32_t));
+        if (g > cap) g = cap;
+        if (g > count) g = count;
+        grid = (int)(g > 0 ? g : 1);
+        err = dev_alloc(ac, (void **)&d_bits, sizeof(uint32_t) * (size_t)(words * grid), stream);
+    }
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(d_nodes, nodes, sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, stream);
     if (err == cudaSuccess)
         err = launch_np_samples(h->d_row_ptr, h->d_col, pos, d_nodes, count, h->d_node_graph,
-                                h->num_graphs > 1 ? h->d_graphs : nullptr, h->n, max_graph, d_out, h->sms * 8, stream);
+                                h->num_graphs > 1 ? h->d_graphs : nullptr, h->n, max_graph, d_out, grid, d_bits, words,
+                                stream);
     std::vector<double> out((size_t)count, 0.0);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
     if (d_nodes) cudaFreeAsync(d_nodes, stream);
     if (d_out) cudaFreeAsync(d_out, stream);
+    if (d_bits) cudaFreeAsync(d_bits, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return err == cudaErrorMemoryAllocation ? fail(SNAP_ERR_OUT_OF_MEMORY, "NP scratch")

@@ -12,8 +12,10 @@
 // (x_i - x_v)^2 + (y_i - y_v)^2 with every operation rounded on its own, so
 // the ranking equals that of an FP64 evaluation of the same positions.
 //
-// One block per sample.  N_G(i) is a bitmap over the graph in shared memory
-// (graphs of up to 2^18 vertices, 32 KB).  The k-th nearest key (squared
+// One block per sample.  N_G(i) is a bitmap over the graph: in shared memory
+// for graphs of up to 2^18 vertices (32 KB), else in a global scratch row of
+// the block's own; a warp marks each neighbour's row (so a hub's row is read
+// by 32 lanes).  The k-th nearest key (squared
 // distance, then id) is found by an exact most-significant-digit radix
 // select: eight 8-bit passes over the distance bits (non-negative doubles
 // order as their bit patterns), then four over the ids of the vertices at
@@ -52,8 +54,11 @@ __global__ void __launch_bounds__(256) np_sample_kernel(const int64_t *__restric
                                                         const int32_t *__restrict__ nodes, int32_t count,
                                                         const int32_t *__restrict__ node_graph,
                                                         const GraphInfo *__restrict__ graphs, int32_t n,
-                                                        double *__restrict__ out) {
-    extern __shared__ uint32_t bits[];
+                                                        double *__restrict__ out, uint32_t *gbits,
+                                                        int64_t gbits_words) {
+    extern __shared__ uint32_t sbits[];
+    uint32_t *bits = gbits ? gbits + (int64_t)blockIdx.x * gbits_words : sbits;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     __shared__ uint32_t hist[256];
     __shared__ uint32_t s_rank, s_k, s_inter;
     __shared__ unsigned long long s_prefix;
@@ -72,12 +77,13 @@ __global__ void __launch_bounds__(256) np_sample_kernel(const int64_t *__restric
             s_inter = 0;
         }
         __syncthreads();
-        // N_G(i): neighbours and their neighbours
+        // N_G(i): neighbours and their neighbours, one warp per neighbour
         const int64_t b0 = row_ptr[i], b1 = row_ptr[i + 1];
-        for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
+        for (int64_t e = b0 + warp; e < b1; e += nwarps) {
             const int32_t u = col_idx[e];
-            atomicOr(&bits[(u - lo) >> 5], 1u << ((u - lo) & 31));
-            for (int64_t f = row_ptr[u]; f < row_ptr[u + 1]; ++f) {
+            if (lane == 0) atomicOr(&bits[(u - lo) >> 5], 1u << ((u - lo) & 31));
+            const int64_t f1 = row_ptr[u + 1];
+            for (int64_t f = row_ptr[u] + lane; f < f1; f += 32) {
                 const int32_t v = col_idx[f] - lo;
                 atomicOr(&bits[v >> 5], 1u << (v & 31));
             }
@@ -163,11 +169,12 @@ __global__ void __launch_bounds__(256) np_sample_kernel(const int64_t *__restric
 
 cudaError_t launch_np_samples(const int64_t *row_ptr, const int32_t *col_idx, const float2 *pos, const int32_t *nodes,
                               int32_t count, const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
-                              int32_t max_graph, double *out, int grid, cudaStream_t s) {
+                              int32_t max_graph, double *out, int grid, uint32_t *gbits, int64_t gbits_words,
+                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = sizeof(uint32_t) * (size_t)((max_graph + 31) / 32);
+    const size_t smem = gbits ? 0 : sizeof(uint32_t) * (size_t)((max_graph + 31) / 32);
     np_sample_kernel<<<grid < count ? grid : count, 256, smem, s>>>(row_ptr, col_idx, pos, nodes, count, node_graph,
-                                                                   graphs, n, out);
+                                                                   graphs, n, out, gbits, gbits_words);
     return cudaGetLastError();
 }
 

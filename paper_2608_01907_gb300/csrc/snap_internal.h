@@ -227,11 +227,15 @@ cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, 
 // Neighbourhood preservation (Section 4.1, r = 2) of `count` sampled
 // vertices: out[q] = the Jaccard index of the 2-hop set and the nearest set
 // of nodes[q], or -1 for a vertex without neighbours.  Every graph (all of
-// [0, n) when graphs is null) has at most max_graph vertices.
+// [0, n) when graphs is null) has at most max_graph vertices.  Graphs of up
+// to kNpMaxGraph vertices keep the 2-hop bitmap in shared memory; larger
+// ones pass gbits, gbits_words words of global scratch per block (grid
+// blocks at most).
 constexpr int32_t kNpMaxGraph = 1 << 18;
 cudaError_t launch_np_samples(const int64_t *row_ptr, const int32_t *col_idx, const float2 *pos, const int32_t *nodes,
                               int32_t count, const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
-                              int32_t max_graph, double *out, int grid, cudaStream_t s);
+                              int32_t max_graph, double *out, int grid, uint32_t *gbits, int64_t gbits_words,
+                              cudaStream_t s);
 cudaError_t launch_objective_pairs_sampled(const float2 *pos, const int32_t *deg, const float4 *wt, int32_t n,
                                            int64_t pairs, uint64_t seed, double *partial, int grid,
                                            cudaStream_t s);

@@ -44,7 +44,7 @@ using namespace snap;
 constexpr int32_t kNoallocMaxNodes = 1 << 18;
 constexpr uint32_t kNoallocBadCsr = 8u;
 constexpr int kMaxDevices = 64;
-constexpr int kSegLen = 32;
+constexpr int kSegLen = 16;
 
 // The scratch.  In host code these names are host-side stand-ins, not device
 // addresses; the device addresses come from cudaGetSymbolAddress below.
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) check_edges_kernel(const int64_t *__restr
     if (bad) atomicOr(status, kNoallocBadCsr);
 }
 
-// Chunk c of S of one synchronous epoch on a validated CSR: 32-edge segments,
+// Chunk c of S of one synchronous epoch on a validated CSR: 16-edge segments,
 // one lane each; the source's terms are summed in registers and flushed once
 // per row run.
 __global__ void __launch_bounds__(256) sync_chunk_noalloc_kernel(const int64_t *__restrict__ row_ptr,

@@ -51,6 +51,29 @@ def test_device_np_equals_oracle_np(cuda, name, mode):
     assert abs(got - ref) < 1e-12
 
 
+def test_device_np_past_the_shared_memory_bitmap(cuda):
+    """A graph above 2^18 vertices (the 2-hop bitmap in global scratch), with
+    the top hub and its neighbours among the samples (rows read by a warp)."""
+    torch = cuda
+    from synth import rmat_graph
+    g = rmat_graph(19, 3_000_000, seed=2)
+    assert g.n > (1 << 18)
+    deg = np.diff(g.row_ptr)
+    hub = int(np.argmax(deg))
+    rng = np.random.default_rng(4)
+    nodes = np.concatenate([[hub], g.col_idx[g.row_ptr[hub]:g.row_ptr[hub] + 20],
+                            rng.choice(g.n, 150, replace=False)]).astype(np.int32)
+    sched = snap.linear_schedule(eta0=1.0, total_epochs=5)
+    Y = gpu_layout(torch, g, initial_positions(g.n, 5), 5, 3, sched, seed=6)
+    pos = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
+    with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(keep_csr=True)) as L:
+        got, used = L.neighborhood_preservation(pos, nodes)
+    ref = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, Y.astype(np.float64), nodes)
+    print(f"device NP on R-MAT 2^19 (hub degree {deg[hub]}): {got:.6f} vs oracle {ref:.6f} over {used} samples")
+    assert used == int((deg[nodes] > 0).sum())
+    assert abs(got - ref) < 1e-12
+
+
 def test_device_np_needs_the_csr(cuda):
     torch = cuda
     g = sbm_graph(n=400, blocks=4, p_in=0.05, p_out=0.005, seed=2)
