@@ -119,9 +119,8 @@ typedef struct {
     int32_t block_threads;    /* threads per block; 0 = default (256) */
     int32_t flags;            /* SNAP_FLAG_* bits */
     float max_inflight;       /* HOGWILD modes: at most this share of the graph's entries in flight at
-                                 once (lanes = share x entries); 0 = default (HOGWILD 0.01,
-                                 HOGWILD_RED 0.005).  Concurrent updates of one vertex degrade Hogwild
-                                 quality on small graphs */
+                                 once (lanes = share x entries); 0 = default (0.005).  Concurrent
+                                 updates of one vertex degrade Hogwild quality on small graphs */
 } snap_options;
 
 /* snap_options.flags: capture the launches of a snap_layout_epochs call with

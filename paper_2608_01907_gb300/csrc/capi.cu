@@ -867,14 +867,17 @@ static snap_status check_schedule(const snap_schedule *s) {
     return SNAP_OK;
 }
 
-// Default share of a graph's entries in flight at once.  Concurrent updates
-// of one vertex cost Hogwild quality; atomic adds of changes computed from
-// the same stale position overshoot where overwrites undershoot, so
-// HOGWILD_RED takes a lower share (LFR 260k / 6.9M, 5 seeds, NP against the
-// oracle: HOGWILD_RED -1.4% at 1%, -0.7% at 0.5%, -0.4% at 0.3%; HOGWILD
-// +0.4% at 1%).  0.5% costs no time on LFR or R-MAT 2^20 (0.3%: 1.4-1.6x
-// slower); on the 34M-edge R-MAT graph every share exceeds the resident lanes.
-static double default_inflight(int red) { return red ? 0.005 : 0.01; }
+// Default share of a graph's entries in flight at once: 0.5% for both modes.
+// Concurrent updates of one vertex cost Hogwild quality: atomic adds of
+// changes computed from the same stale position overshoot, overwrites lose
+// updates (LFR 260k / 6.9M, 5 seeds, NP against the oracle: HOGWILD_RED
+// -1.4% at 1%, -0.7% at 0.5%, -0.4% at 0.3%; 30 epochs, SI of the planted
+// communities against the oracle's, mean of 3 runs: HOGWILD -5.7% at 1%,
+// -3.7% at 0.5% and at 0.25%; HOGWILD_RED -3.6% at 0.5%, -2.0% at 0.25%).
+// 0.5% costs HOGWILD 6% of the LFR epoch and HOGWILD_RED none (0.25%:
+// 1.5x slower); on the 34M-edge R-MAT graph every share exceeds the
+// resident lanes.
+static double default_inflight(int) { return 0.005; }
 
 // Grid of a HOGWILD epoch: enough blocks for every chunk, at most the
 // resident maximum, and at most max_inflight * entries lanes (one entry in

@@ -7,7 +7,8 @@ tests/golden/make_convergence_lfr.py from the oracle alone).
 Section 4.3 reports the lock-free variants within [-5%, 5%] of the serial
 algorithm in SI and NP; after 30 epochs both GPU modes must be within that
 band in SI and within 2% in NP, and SI must rise from 10 to 30 epochs as it
-does for the oracle."""
+does for the oracle.  The GPU side is the mean of three runs: the lock-free
+modes' races differ from run to run (SI spread about 0.01 at T = 30)."""
 import multiprocessing as mp
 import os
 import sys
@@ -37,16 +38,21 @@ def test_gpu_convergence_in_T_matches_oracle(cuda, mode, tmp_path):
     ref = {int(r[0]): (float(r[1]), float(r[2])) for r in read_golden("convergence_lfr.txt")}
     g = lfr260k()
     paths = []
+    runs = 3   # the racy modes' layouts differ from run to run: the scores are means over 3 runs
     with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(mode=mode)) as L:
         for T in mc.TS:
-            pos = torch.from_numpy(initial_positions(g.n, mc.SEED)).cuda()
-            L.epochs(pos, 0, T, mc.K, snap.linear_schedule(1.0, T), mc.SEED)
-            L.check()
-            p = str(tmp_path / f"T{T}.npy")
-            np.save(p, pos.cpu().numpy().astype(np.float64))
-            paths.append(p)
+            for run in range(runs):
+                pos = torch.from_numpy(initial_positions(g.n, mc.SEED)).cuda()
+                L.epochs(pos, 0, T, mc.K, snap.linear_schedule(1.0, T), mc.SEED)
+                L.check()
+                p = str(tmp_path / f"T{T}_{run}.npy")
+                np.save(p, pos.cpu().numpy().astype(np.float64))
+                paths.append(p)
     with mp.get_context("spawn").Pool(len(paths)) as pool:
-        got = dict(zip(mc.TS, pool.map(_score, paths)))
+        scores = np.array(pool.map(_score, paths)).reshape(len(mc.TS), runs, 2)
+    got = {T: scores[q].mean(axis=0) for q, T in enumerate(mc.TS)}
+    print(f"LFR mode={mode} SI per run: " + "; ".join(f"T={T}: " + " ".join(f"{x:.4f}" for x in scores[q, :, 0])
+                                                         for q, T in enumerate(mc.TS)))
     for T in mc.TS:
         print(f"LFR mode={mode} T={T}: SI {got[T][0]:.4f} vs oracle {ref[T][0]:.4f} "
               f"({got[T][0] / ref[T][0] - 1:+.2%}), NP {got[T][1]:.4f} vs {ref[T][1]:.4f} "
