@@ -567,7 +567,7 @@ def run_snap(args, rank, world, local_rank):
     # hardware ceilings measured now, on an array the size of the positions
     probes = probe_rates(8 * n, stream) if not args.no_probe else None
     peak, peak_kind = measured_peak()
-    kname = (f"oriented_epoch_kernel<RED={int(mode == snap.MODE_HOGWILD_RED)},G={min(k, 4)}>"
+    kname = (f"oriented_epoch_kernel<RED={int(mode == snap.MODE_HOGWILD_RED)},GW={k if k <= 4 else 5}>"
              if mode != snap.MODE_SYNC else "sync epoch (sync_chunk_kernel + sync_apply_kernel)")
     roofs = rooflines(nnz, n, k, float(np.mean(launch_ms)), probes, peak, peak_kind,
                       recorded_traffic(args.mode, k), kname, sync=mode == snap.MODE_SYNC)
@@ -699,7 +699,7 @@ def batch_result(args, local_rank, steps, warmup):
     peak, peak_kind = measured_peak()
     probes = probe_rates(8 * n, stream) if not args.no_probe else None
     roofs = rooflines(nnz, n, k, launch_ms, probes, peak, peak_kind, None,
-                      f"oriented_epoch_kernel<RED=1,G={min(k, 4)},MULTI=1>")
+                      f"oriented_epoch_kernel<RED=1,GW={k if k <= 4 else 5},MULTI=1>")
 
     # one graph per handle and per launch, on a seeded sample of the graphs
     rng = np.random.default_rng(args.seed)
