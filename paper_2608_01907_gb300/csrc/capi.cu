@@ -1325,14 +1325,16 @@ static snap_status np_impl(snap_layout *h, const float2 *pos, const int32_t *nod
     cudaError_t err = dev_alloc(ac, (void **)&d_nodes, sizeof(int32_t) * (size_t)count, stream);
     if (err == cudaSuccess) err = dev_alloc(ac, (void **)&d_out, sizeof(double) * (size_t)count, stream);
     if (err == cudaSuccess && max_graph > kNpMaxGraph) {
-        // 2-hop bitmaps in global scratch: one row per block, at most 1 GiB in all
+        // 2-hop bitmaps and candidate lists in global scratch, one of each per block,
+        // at most 1 GiB in all
         words = ((int64_t)max_graph + 31) / 32;
         int64_t g = (int64_t)h->sms * 2;
-        const int64_t cap = ((int64_t)1 << 30) / (words * (int64_t)sizeof(uint32_t));
+        const int64_t per_block = (words + 1 + 3 * kNpCandidates) * (int64_t)sizeof(uint32_t);
+        const int64_t cap = ((int64_t)1 << 30) / per_block;
         if (g > cap) g = cap;
         if (g > count) g = count;
         grid = (int)(g > 0 ? g : 1);
-        err = dev_alloc(ac, (void **)&d_bits, sizeof(uint32_t) * (size_t)(words * grid), stream);
+        err = dev_alloc(ac, (void **)&d_bits, sizeof(uint32_t) * (size_t)np_scratch_words(words, grid), stream);
     }
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(d_nodes, nodes, sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, stream);

@@ -229,9 +229,14 @@ cudaError_t launch_objective_pairs_batch(const float2 *pos, const int32_t *deg, 
 // of nodes[q], or -1 for a vertex without neighbours.  Every graph (all of
 // [0, n) when graphs is null) has at most max_graph vertices.  Graphs of up
 // to kNpMaxGraph vertices keep the 2-hop bitmap in shared memory; larger
-// ones pass gbits, gbits_words words of global scratch per block (grid
-// blocks at most).
+// ones pass gbits, np_scratch_words(gbits_words, grid) words of global
+// scratch: a bitmap row of gbits_words words per block, then per block a
+// list of kNpCandidates keys (8 bytes) and ids (4 bytes).
 constexpr int32_t kNpMaxGraph = 1 << 18;
+constexpr int64_t kNpCandidates = 1 << 16;
+inline int64_t np_scratch_words(int64_t gbits_words, int64_t grid) {
+    return ((grid * gbits_words + 1) & ~(int64_t)1) + grid * kNpCandidates * 3;
+}
 cudaError_t launch_np_samples(const int64_t *row_ptr, const int32_t *col_idx, const float2 *pos, const int32_t *nodes,
                               int32_t count, const int32_t *node_graph, const GraphInfo *graphs, int32_t n,
                               int32_t max_graph, double *out, int grid, uint32_t *gbits, int64_t gbits_words,

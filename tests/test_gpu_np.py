@@ -72,6 +72,16 @@ def test_device_np_past_the_shared_memory_bitmap(cuda):
     print(f"device NP on R-MAT 2^19 (hub degree {deg[hub]}): {got:.6f} vs oracle {ref:.6f} over {used} samples")
     assert used == int((deg[nodes] > 0).sum())
     assert abs(got - ref) < 1e-12
+    # every vertex at one of two points: all distances tie within a factor of two,
+    # so the candidate list overflows and the select runs over all vertices
+    Y2 = np.zeros((g.n, 2), np.float32)
+    Y2[::3] = (0.5, 0.25)
+    pos2 = torch.from_numpy(Y2).cuda()
+    with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(keep_csr=True)) as L:
+        got2, _ = L.neighborhood_preservation(pos2, nodes[:40])
+    ref2 = oracle.neighborhood_preservation(g.row_ptr, g.col_idx, g.n, Y2.astype(np.float64), nodes[:40])
+    print(f"device NP with tied distances: {got2:.6f} vs oracle {ref2:.6f}")
+    assert abs(got2 - ref2) < 1e-12
 
 
 def test_device_np_needs_the_csr(cuda):
