@@ -183,15 +183,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(mode, k):
+def recorded_traffic(mode, k, workload, sampler):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source for this workload and sampler (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         e = rec.get(f"{mode}_k{k}")
-        if e and e.get("source_hash") == kernel_source_hash():
+        if (e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == workload
+                and e.get("sampler") == sampler):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -570,7 +571,8 @@ def run_snap(args, rank, world, local_rank):
     kname = (f"oriented_epoch_kernel<RED={int(mode == snap.MODE_HOGWILD_RED)},GW={k if k <= 4 else 5}>"
              if mode != snap.MODE_SYNC else "sync epoch (sync_chunk_kernel + sync_apply_kernel)")
     roofs = rooflines(nnz, n, k, float(np.mean(launch_ms)), probes, peak, peak_kind,
-                      recorded_traffic(args.mode, k), kname, sync=mode == snap.MODE_SYNC)
+                      recorded_traffic(args.mode, k, workload_config(args, n, nnz, 0)["workload"], args.sampler), kname,
+                      sync=mode == snap.MODE_SYNC)
     if probes and "mode_sync" in extras:
         # the whole synchronous epoch (16 chunk launches + 16 applies) against its access mix's ceiling
         t_mix = nnz * (1 + k) / probes["random_load_int64_atomic_triples_per_s"]

@@ -81,3 +81,21 @@ def test_rooflines_follow_their_definitions():
     probes["random_load_int64_atomic_triples_per_s"] = 50e9
     r = bench.rooflines(nnz, n, k, ms, probes, 6689.1, "measured", None, "kernel", sync=True)
     assert abs(r["ops"]["mixed_frac"] - ops / 50e9 / (ms / 1e3)) < 1e-12
+
+
+def test_recorded_traffic_only_for_its_workload_and_source():
+    """The DRAM bytes recorded by an ncu capture apply only to the workload,
+    sampler and kernel source they were taken on."""
+    import json
+    import os
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    e = rec["hogwild_red_k3"]
+    got = bench.recorded_traffic("hogwild_red", 3, e["workload"], e["sampler"])
+    if e["source_hash"] == bench.kernel_source_hash():
+        assert got == float(e["dram_bytes_per_launch"])
+    else:
+        assert got is None
+    assert bench.recorded_traffic("hogwild_red", 3, "rmat21-17000000e-k3-30ep-bfs", e["sampler"]) is None
+    assert bench.recorded_traffic("hogwild_red", 3, e["workload"], "degree") is None
+    assert bench.recorded_traffic("hogwild_red", 5, e["workload"], e["sampler"]) is None
