@@ -7,8 +7,9 @@ tests/golden/make_convergence_lfr.py from the oracle alone).
 Section 4.3 reports the lock-free variants within [-5%, 5%] of the serial
 algorithm in SI and NP; after 30 epochs both GPU modes must be within that
 band in SI and within 2% in NP, and SI must rise from 10 to 30 epochs as it
-does for the oracle.  The GPU side is the mean of five runs: the lock-free
-modes' races differ from run to run (SI spread about 0.01 at T = 30)."""
+does for the oracle.  The GPU side is a mean over runs (8 at T = 30, 3 at
+T = 10): the lock-free modes' races differ from run to run (SI spread about
+0.009 at T = 30)."""
 import multiprocessing as mp
 import os
 import sys
@@ -37,22 +38,30 @@ def test_gpu_convergence_in_T_matches_oracle(cuda, mode, tmp_path):
     torch = cuda
     ref = {int(r[0]): (float(r[1]), float(r[2])) for r in read_golden("convergence_lfr.txt")}
     g = lfr260k()
-    paths = []
-    runs = 5   # the racy modes' layouts differ from run to run: the scores are means over 5 runs
+    # the racy modes' layouts differ from run to run (SI spread about 0.009 at
+    # T = 30): the scores are means over several runs, 8 at T = 30 where the
+    # band is asserted, 3 at T = 10
+    runs = {10: 3, 30: 8}
+    paths = {T: [] for T in mc.TS}
     with snap.Layout(g.row_ptr, g.col_idx, opts=snap.make_options(mode=mode)) as L:
         for T in mc.TS:
-            for run in range(runs):
+            for run in range(runs[T]):
                 pos = torch.from_numpy(initial_positions(g.n, mc.SEED)).cuda()
                 L.epochs(pos, 0, T, mc.K, snap.linear_schedule(1.0, T), mc.SEED)
                 L.check()
                 p = str(tmp_path / f"T{T}_{run}.npy")
                 np.save(p, pos.cpu().numpy().astype(np.float64))
-                paths.append(p)
-    with mp.get_context("spawn").Pool(len(paths)) as pool:
-        scores = np.array(pool.map(_score, paths)).reshape(len(mc.TS), runs, 2)
-    got = {T: scores[q].mean(axis=0) for q, T in enumerate(mc.TS)}
-    print(f"LFR mode={mode} SI per run: " + "; ".join(f"T={T}: " + " ".join(f"{x:.4f}" for x in scores[q, :, 0])
-                                                         for q, T in enumerate(mc.TS)))
+                paths[T].append(p)
+    flat = [p for T in mc.TS for p in paths[T]]
+    with mp.get_context("spawn").Pool(min(len(flat), 12)) as pool:
+        flat_scores = pool.map(_score, flat)
+    scores, at = {}, 0
+    for T in mc.TS:
+        scores[T] = np.array(flat_scores[at:at + runs[T]])
+        at += runs[T]
+    got = {T: scores[T].mean(axis=0) for T in mc.TS}
+    print(f"LFR mode={mode} SI per run: " + "; ".join(f"T={T}: " + " ".join(f"{x:.4f}" for x in scores[T][:, 0])
+                                                         for T in mc.TS))
     for T in mc.TS:
         print(f"LFR mode={mode} T={T}: SI {got[T][0]:.4f} vs oracle {ref[T][0]:.4f} "
               f"({got[T][0] / ref[T][0] - 1:+.2%}), NP {got[T][1]:.4f} vs {ref[T][1]:.4f} "
