@@ -87,7 +87,7 @@ def test_sync_is_bitwise_deterministic_and_resumable(cuda):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("mode", [snap.MODE_HOGWILD, snap.MODE_HOGWILD_RED])
 @pytest.mark.parametrize("n,m,k", [(2, 0, 0), (2, 0, 1), (5, 6, 3), (12, 30, 5), (40, 120, 3), (90, 300, 10),
-                                   (300, 900, 4), (60, 0, 2)])
+                                   (300, 900, 4), (60, 0, 2), (90, 300, 33), (200, 700, 64)])
 def test_single_lane_hogwild_is_algorithm1_in_oriented_order(cuda, mode, n, m, k):
     g = _two_node() if n == 2 else tiny_graph(n, m, seed=n)
     assert g.nnz // 2 <= 4096
