@@ -147,9 +147,11 @@ __device__ __forceinline__ int4 make_entry(int32_t i, int32_t j, int64_t fwd, in
 // direction many times in a row.  Sequential FP64 emulation on R-MAT 2^22,
 // 4-entry chunks: objective +1.5% / NP -2.0% against the shuffled order of
 // Algorithm 1 in ascending order, +0.9% / -0.7% with the rows permuted.)
-__device__ __forceinline__ int64_t gcd_dev(int64_t a, int64_t b) {
+// (32-bit arithmetic: a row has fewer than 2^31 entries, and 64-bit
+// remainders cost several times as much on the GPU.)
+__device__ __forceinline__ uint32_t gcd_dev(uint32_t a, uint32_t b) {
     while (b) {
-        const int64_t t = a % b;
+        const uint32_t t = a % b;
         a = b;
         b = t;
     }
@@ -157,9 +159,9 @@ __device__ __forceinline__ int64_t gcd_dev(int64_t a, int64_t b) {
 }
 
 __device__ __forceinline__ int64_t row_multiplier(int32_t L) {
-    int64_t a = (int64_t)(0.6180339887498949 * (double)L) | 1;
-    while (gcd_dev(a, L) != 1) a += 2;
-    return a;
+    uint32_t a = (uint32_t)(int64_t)(0.6180339887498949 * (double)L) | 1u;
+    while (gcd_dev(a, (uint32_t)L) != 1u) a += 2u;
+    return (int64_t)a;
 }
 
 __device__ __forceinline__ int32_t row_position(int32_t q, int32_t L) {
